@@ -1,0 +1,179 @@
+/*
+ * emd_gb300.h -- C ABI of the GB300 (sm_103a) dynamic-formulation EMD misfit library.
+ *
+ * The library computes the earth mover's distance between an observed and a predicted
+ * seismic gather on an nr x nt grid (receivers x time), as defined in Sec. 2.1-2.2 of
+ * arXiv 1808.07284: the gathers are compared through the Mainini recombination
+ * mu = Pcal+ + Pobs-, nu = Pobs+ + Pcal- (Sec. 2.1), and the distance is
+ *     min_u ||u||_{1,1} + eps/2 ||u||_2^2   s.t.  div u + Pcal - Pobs = 0,  zero boundary flux
+ * times dx*dt, solved by PDHG with linesearch (Algorithm 1).  The solver returns the
+ * distance, the dual potential phi (the adjoint source, Sec. 2.3) and the flux m = u.
+ *
+ * Conventions shared by every entry point:
+ *  - Grids are row-major [nr][nt]: element (i, j) sits at i*nt + j; i = receiver
+ *    (spacing dx), j = time sample (spacing dt, contiguous).  The flux m is [2][nr][nt]:
+ *    the x (receiver) component plane first, then the t (time) plane.
+ *  - Every array argument is a DEVICE pointer owned by the caller, FP32, unless stated
+ *    otherwise.  The library never allocates device memory: scratch space is the
+ *    caller's `workspace` (device, 256-byte aligned, size from the *_workspace_size
+ *    queries) and is only valid for the duration of the call.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default stream).
+ *    Calls that return host results (emd_result, masses) synchronise that stream
+ *    before returning.
+ *  - Every call validates its arguments and returns EMD_ERR_ARG without launching
+ *    anything when they are invalid (nt >= 2, nr >= 1, dt > 0, dx > 0 and finite,
+ *    0 < xi < 1, 0 < zeta < 1, delta > 0, eps >= 0, max_iter >= 1, non-null pointers).
+ *    Device-side failures (non-finite iterates, a linesearch that never passes) come
+ *    back as a status, never as a trap; a CUDA error is EMD_ERR_CUDA.
+ *  - No entry point is reentrant on the same workspace: calls that share a workspace
+ *    must be ordered (same stream, or synchronised).
+ */
+#ifndef EMD_GB300_H
+#define EMD_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without requiring the CUDA headers. */
+typedef struct CUstream_st *emd_stream_t;
+
+typedef enum {
+  EMD_OK = 0,
+  EMD_ERR_ARG = 1,        /* invalid argument; nothing was launched                      */
+  EMD_ERR_CUDA = 2,       /* a CUDA runtime call failed (launch, copy, sync)             */
+  EMD_ERR_NONFINITE = 3,  /* an inner product became NaN/Inf (e.g. NaN in the inputs)    */
+  EMD_ERR_LINESEARCH = 4, /* Algorithm 1's backtracking did not pass in ls_max_trials    */
+  EMD_ERR_TIMEOUT = 5,    /* reserved: a bounded device-side wait ran out                */
+  EMD_ERR_WORKSPACE = 6   /* workspace NULL, too small or not 256-byte aligned           */
+} emd_status;
+
+typedef enum {
+  EMD_BAL_NONE = 0, /* solve with f = Pcal - Pobs as printed (infeasible if sum f != 0)   */
+  EMD_BAL_MEAN = 1  /* remove the mean of f first, so that the zero-flux problem is feasible */
+} emd_balance;
+
+/*
+ * Solver parameters (Sec. 2.2 and Algorithm 1).  emd_default_params() fills the paper's
+ * constants: eps = 1e-4, xi = 0.5, zeta = 0.99, delta = 1e5, plus max_iter = 2000,
+ * tol = 0, check_every = 10, ls_max_trials = 40, linesearch = 1, ls_norm = 2,
+ * balance = EMD_BAL_MEAN, no warm start, tile = 0, launch_mode = 0.
+ */
+typedef struct {
+  double eps;        /* regularisation epsilon of Phi = ||u||_{1,1} + eps/2 ||u||^2      */
+  double xi;         /* backtracking factor of the linesearch, in (0, 1)                 */
+  double zeta;       /* linesearch test constant, in (0, 1)                              */
+  double delta;      /* dual/primal step ratio: beta = delta * alpha                     */
+  double alpha0;     /* first primal step; <= 0 selects 1/sqrt(delta*lambda) with the
+                        bound lambda = 4/dx^2 + 4/dt^2 (4/dt^2 when nr == 1); with
+                        linesearch == 0 it selects alpha = beta = 1/sqrt(lambda)         */
+  double tol;        /* stop when max(||div u + f|| / ||f||, ||u^{k+1}-u^k|| / ||u^{k+1}||)
+                        <= tol, tested every check_every iterations; 0 = run max_iter    */
+  int max_iter;      /* cap on accepted PDHG iterations (>= 1)                           */
+  int check_every;   /* iterations between stopping tests (>= 1)                         */
+  int ls_max_trials; /* backtracking trials per iteration before EMD_ERR_LINESEARCH       */
+  int linesearch;    /* 1: Algorithm 1; 0: fixed-step PDHG with ubar = 2u^{k+1} - u^k    */
+  int ls_norm;       /* norm of the linesearch test; only 2 (Euclidean) is implemented   */
+  int balance;       /* emd_balance                                                      */
+  const float *phi_init; /* optional warm start for phi, device [nr][nt]; NULL = zeros   */
+  const float *m_init;   /* optional warm start for u, device [2][nr][nt]; NULL = zeros  */
+  int tile;          /* stencil tile-shape id (emd_tile_count() of them); 0 = automatic  */
+  int launch_mode;   /* 0: passes replayed from a captured CUDA graph; 1: plain launches */
+  int debug_fault;   /* fault injection for tests: 0 = off, 1 = every linesearch trial
+                        fails (exercises EMD_ERR_LINESEARCH); never set in production   */
+} emd_params;
+
+/* Host-side result of one solve.  Distances are in the units of dx*dt*|u|. */
+typedef struct {
+  double dist;        /* dx*dt*Phi(u): the EMD misfit as defined in Sec. 2.2             */
+  double dist_l1;     /* dx*dt*||u||_{1,1}: the same without the eps term                */
+  double mass_mu;     /* dx*dt*sum(mu), mu = Pcal+ + Pobs-                               */
+  double mass_nu;     /* dx*dt*sum(nu), nu = Pobs+ + Pcal-                               */
+  double imbalance;   /* mass_mu - mass_nu = dx*dt*sum(Pcal - Pobs)                     */
+  double residual;    /* max(r_feas, r_step) after the last iteration                    */
+  double r_feas;      /* ||div u + f||_2 / ||f||_2                                       */
+  double r_step;      /* ||u^{k+1} - u^k||_2 / ||u^{k+1}||_2                             */
+  double duality_gap; /* dx*dt*(Phi(u) - <phi,f> + sum h*(grad phi)), h* the conjugate of
+                         |v| + eps/2 v^2; tends to 0 at the saddle point                 */
+  double alpha;       /* last accepted primal step alpha_k                               */
+  double theta;       /* last theta_k                                                    */
+  int iters;          /* accepted PDHG iterations                                        */
+  int ls_trials;      /* linesearch trials in total (>= iters)                           */
+  int status;         /* emd_status of this solve                                        */
+} emd_result;
+
+/* Fills *p with the defaults listed above.  p must not be NULL. */
+void emd_default_params(emd_params *p);
+
+/* Number of stencil tile shapes compiled into the library (valid ids: 1..count). */
+int emd_tile_count(void);
+
+/* Bytes of device workspace emd_dyn_solve needs for one nr x nt gather (0 if invalid). */
+size_t emd_workspace_size(int nt, int nr);
+
+/*
+ * Mainini decomposition and recombination (Sec. 2.1).
+ * Inputs f_obs, f_pred: device [nr][nt].  Outputs (each nullable): mu, nu device
+ * [nr][nt] with mu = Pcal+ + Pobs-, nu = Pobs+ + Pcal-; masses (HOST, 2 doubles)
+ * = {dx*dt*sum(mu), dx*dt*sum(nu)} accumulated in FP64 (dt alone when nr == 1).
+ * Needs emd_workspace_size(nt, nr) bytes of workspace (only a few KB are touched).
+ * Synchronises `stream` when masses != NULL.
+ */
+emd_status emd_decompose(const float *f_obs, const float *f_pred, int nt, int nr, double dt,
+                         double dx, float *mu, float *nu, double *masses, void *workspace,
+                         size_t ws_bytes, emd_stream_t stream);
+
+/*
+ * One EMD solve: Algorithm 1 (PDHG with linesearch) on f = Pcal - Pobs (Sec. 2.2).
+ * Inputs f_obs (Pobs), f_pred (Pcal): device [nr][nt].  params: host pointer (NULL =
+ * defaults).  Outputs: phi device [nr][nt] (the dual potential after the last
+ * iteration), m device [2][nr][nt] (the flux u), result HOST (required).
+ * Iterates are FP32; the linesearch inner products, the stopping residual, the mass
+ * sums and the distance accumulate in FP64.  Returns the solve's status (also in
+ * result->status).  Synchronises `stream`.
+ */
+emd_status emd_dyn_solve(const float *f_obs, const float *f_pred, int nt, int nr, double dt,
+                         double dx, const emd_params *params, float *phi, float *m,
+                         emd_result *result, void *workspace, size_t ws_bytes,
+                         emd_stream_t stream);
+
+/* Bytes of workspace for emd_dyn_solve_batched over B gathers of sizes nt[b] x nr[b]
+ * (host arrays).  0 if any size is invalid. */
+size_t emd_batched_workspace_size(int B, const int *nt, const int *nr);
+
+/*
+ * B independent solves (the paper solves one EMD per shot) in one launch per PDHG
+ * iteration over all gathers, each gather with its own linesearch state; gathers
+ * that meet tol stop while the rest go on.  All arrays of pointers and sizes are HOST
+ * arrays of length B; the pointers they hold are device pointers with the layouts of
+ * emd_dyn_solve.  params apply to every gather (its warm-start pointers must be NULL).
+ * results: HOST array of B.  Returns EMD_OK if every gather succeeded, else the first
+ * non-OK status (each gather's own status is in results[b].status).
+ */
+emd_status emd_dyn_solve_batched(int B, const float *const *f_obs, const float *const *f_pred,
+                                 const int *nt, const int *nr, const double *dt,
+                                 const double *dx, const emd_params *params,
+                                 float *const *phi, float *const *m, emd_result *results,
+                                 void *workspace, size_t ws_bytes, emd_stream_t stream);
+
+/*
+ * Adjoint source of the returned distance (Sec. 2.3: d f_OT / d Pcal = phi).
+ * With dist = dx*dt*Phi, d dist / d Pcal = g * dx*dt * (phi - mean(phi)) when
+ * balance == EMD_BAL_MEAN (phi - 0 otherwise), g = *grad_out (device FP32 scalar; NULL
+ * means 1).  grad_pred receives it, grad_obs (nullable) its negative; both device
+ * [nr][nt].  Needs emd_workspace_size(nt, nr) bytes of workspace.  Does not synchronise.
+ */
+emd_status emd_adjoint(const float *phi, int nt, int nr, double dt, double dx, int balance,
+                       const float *grad_out, float *grad_pred, float *grad_obs,
+                       void *workspace, size_t ws_bytes, emd_stream_t stream);
+
+/* Static, human-readable name of a status code. */
+const char *emd_status_string(emd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMD_GB300_H */

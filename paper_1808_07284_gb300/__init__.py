@@ -1,0 +1,109 @@
+"""GB300-native dynamic-formulation EMD misfit (arXiv 1808.07284).
+
+The earth mover's distance between an observed and a predicted seismic gather
+(receivers x time), compared through the Mainini recombination of Sec. 2.1 and solved
+as the dynamic L1 transport problem of Sec. 2.2 by PDHG with linesearch (Algorithm 1),
+in hand-written sm_103a CUDA behind the C ABI of ``include/emd_gb300.h``.  PyTorch
+provides device memory, streams and autograd; every step of the method runs in the
+library's kernels.
+
+    dist, phi, m, info = emd(f_obs, f_pred, dt, dx, max_iter=2000)
+    loss = emd_loss(f_pred, f_obs, dt, dx)      # differentiable w.r.t. both gathers
+"""
+
+from __future__ import annotations
+
+from ._binding import (  # noqa: F401
+    EMD_BAL_MEAN, EMD_BAL_NONE, EMD_ERR_ARG, EMD_ERR_CUDA, EMD_ERR_LINESEARCH,
+    EMD_ERR_NONFINITE, EMD_ERR_TIMEOUT, EMD_ERR_WORKSPACE, EMD_OK, EXPORTS,
+    EmdError, EmdParams, EmdResult, emd_adjoint, emd_batched_workspace_size, emd_decompose,
+    emd_default_params, emd_dyn_solve, emd_dyn_solve_batched, emd_status_string,
+    emd_tile_count, emd_workspace_size, lib, new_workspace,
+)
+
+__all__ = [
+    "emd", "emd_batched", "emd_loss", "EMDFunction", "emd_decompose", "emd_dyn_solve",
+    "emd_dyn_solve_batched", "emd_adjoint", "emd_default_params", "emd_workspace_size",
+    "emd_batched_workspace_size", "emd_status_string", "emd_tile_count", "EmdError",
+]
+
+
+def emd(f_obs, f_pred, dt, dx, workspace=None, stream=None, check=True, **params):
+    """One EMD solve.  Returns ``(dist, phi[nr, nt], m[2, nr, nt], info)``.
+
+    ``params`` are ``emd_params`` fields (eps, xi, zeta, delta, alpha0, tol, max_iter,
+    check_every, ls_max_trials, linesearch, balance, phi_init, m_init, tile, launch_mode).
+    """
+    import torch
+    nr, nt = f_obs.shape
+    p = emd_default_params(**params)
+    phi = torch.empty((nr, nt), dtype=torch.float32, device=f_obs.device)
+    m = torch.empty((2, nr, nt), dtype=torch.float32, device=f_obs.device)
+    ws = workspace if workspace is not None else new_workspace(emd_workspace_size(nt, nr), f_obs.device)
+    res = emd_dyn_solve(f_obs, f_pred, float(dt), float(dx), p, phi, m, ws, stream, check=check)
+    return res.dist, phi, m, res.as_dict()
+
+
+def emd_batched(f_obs, f_pred, dts, dxs, workspace=None, stream=None, check=True, **params):
+    """B independent solves in one launch per iteration.  Lists in, lists out:
+    ``(dists, phis, ms, infos)``."""
+    import torch
+    B = len(f_obs)
+    dts = [float(v) for v in (dts if hasattr(dts, "__len__") else [dts] * B)]
+    dxs = [float(v) for v in (dxs if hasattr(dxs, "__len__") else [dxs] * B)]
+    p = emd_default_params(**params)
+    phis = [torch.empty_like(t) for t in f_obs]
+    ms = [torch.empty((2,) + tuple(t.shape), dtype=torch.float32, device=t.device) for t in f_obs]
+    nts, nrs = [int(t.shape[1]) for t in f_obs], [int(t.shape[0]) for t in f_obs]
+    ws = workspace if workspace is not None else new_workspace(
+        emd_batched_workspace_size(nts, nrs), f_obs[0].device)
+    res = emd_dyn_solve_batched(f_obs, f_pred, dts, dxs, p, phis, ms, ws, stream, check=check)
+    return [r.dist for r in res], phis, ms, [r.as_dict() for r in res]
+
+
+def _autograd_function():
+    import torch
+
+    class EMDFunction(torch.autograd.Function):
+        """dist = EMD(f_pred, f_obs); backward returns the adjoint source of Sec. 2.3,
+        dx dt (phi - mean phi), from the phi kept by forward (no recomputation)."""
+
+        @staticmethod
+        def forward(ctx, f_pred, f_obs, dt, dx, params):
+            dist, phi, _m, info = emd(f_obs.detach().contiguous(), f_pred.detach().contiguous(),
+                                      dt, dx, **params)
+            ctx.save_for_backward(phi)
+            ctx.dt, ctx.dx = float(dt), float(dx)
+            ctx.balance = params.get("balance", EMD_BAL_MEAN)
+            ctx.info = info
+            return torch.tensor(dist, dtype=torch.float32, device=f_pred.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (phi,) = ctx.saved_tensors
+            nr, nt = phi.shape
+            gp = torch.empty_like(phi)
+            go = torch.empty_like(phi)
+            ws = new_workspace(emd_workspace_size(nt, nr), phi.device)
+            g = grad_out.detach().to(torch.float32).contiguous()
+            emd_adjoint(phi, ctx.dt, ctx.dx, ctx.balance, g, gp, go, ws)
+            return gp, go, None, None, None
+
+    return EMDFunction
+
+
+_EMDFunction = None
+
+
+def __getattr__(name):
+    global _EMDFunction
+    if name == "EMDFunction":
+        if _EMDFunction is None:
+            _EMDFunction = _autograd_function()
+        return _EMDFunction
+    raise AttributeError(name)
+
+
+def emd_loss(f_pred, f_obs, dt, dx, **params):
+    """Differentiable EMD misfit (a 0-dim float32 tensor) with the library's adjoint source."""
+    return __getattr__("EMDFunction").apply(f_pred, f_obs, dt, dx, params)

@@ -1,0 +1,446 @@
+// Host side of the C ABI declared in include/emd_gb300.h: argument checks, workspace
+// layout, the launch sequence of a solve (prepare -> one fused pass per PDHG iteration
+// -> finalize) and result read-back.  All device work is in emd_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "emd_gb300.h"
+#include "emd_kernels.cuh"
+
+namespace {
+
+using emd::Ctl;
+using emd::kThreads;
+using emd::Shot;
+using emd::State;
+
+#define EMD_CK(x)                                  \
+  do {                                             \
+    cudaError_t e_ = (x);                          \
+    if (e_ != cudaSuccess) {                       \
+      (void)cudaGetLastError();                    \
+      return EMD_ERR_CUDA;                         \
+    }                                              \
+  } while (0)
+
+// Stencil tile shapes (TI rows x (W - 8) time samples per CTA); id = index + 1.
+struct Shape {
+  int ti, w;
+  void (*iter)(Ctl);
+  void (*fin)(Ctl);
+};
+
+#define EMD_SHAPE(TI, W) \
+  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true> }
+const Shape kShapes[] = {EMD_SHAPE(16, 128), EMD_SHAPE(8, 128), EMD_SHAPE(32, 128),
+                         EMD_SHAPE(8, 256),  EMD_SHAPE(16, 256), EMD_SHAPE(1, 256)};
+#undef EMD_SHAPE
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+size_t smem_bytes(const Shape &s) { return sizeof(float) * 6u * (s.ti + 4) * s.w; }
+
+size_t align256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
+int ntp_of(int nt) { return (nt + 31) / 32 * 32; }
+int tiles_of(const Shape &s, int nt, int nr) {
+  return ((nr + s.ti - 1) / s.ti) * ((nt + (s.w - 8) - 1) / (s.w - 8));
+}
+
+bool size_ok(int nt, int nr) {
+  if (nt < 2 || nr < 1 || nt > (1 << 24) || nr > (1 << 20)) return false;
+  return static_cast<long long>(nr) * ntp_of(nt) < (1ll << 30);
+}
+
+// Workspace: [states | shots | accumulators | tile_shot | n_done + scratch] then, per gather, the
+// pitched planes f, u0 (x,t), u1 (x,t), u2 (x,t), phi0, phi1 (36 bytes per cell).
+struct Layout {
+  size_t states, shots, acc, tiles, misc, header, total;
+  std::vector<size_t> gather;  // offset of each gather's planes
+  std::vector<size_t> plane;   // bytes of one plane (256-aligned)
+  int max_tiles;
+};
+
+Layout layout(int B, const int *nt, const int *nr) {
+  Layout L{};
+  L.max_tiles = 0;
+  for (int b = 0; b < B; ++b) {
+    int mt = 0;
+    for (const Shape &s : kShapes) mt = std::max(mt, tiles_of(s, nt[b], nr[b]));
+    L.max_tiles += mt;
+  }
+  L.states = 0;
+  L.shots = align256(sizeof(State) * B);
+  L.acc = L.shots + align256(sizeof(Shot) * B);
+  L.tiles = L.acc + align256(sizeof(double) * emd::kSpread * emd::kAcc * B);
+  L.misc = L.tiles + align256(sizeof(int) * static_cast<size_t>(L.max_tiles));
+  L.header = L.misc + 256;
+  size_t off = L.header;
+  for (int b = 0; b < B; ++b) {
+    const size_t pl = align256(sizeof(float) * static_cast<size_t>(nr[b]) * ntp_of(nt[b]));
+    L.gather.push_back(off);
+    L.plane.push_back(pl);
+    off += 9 * pl;
+  }
+  L.total = off;
+  return L;
+}
+
+bool params_ok(const emd_params &p) {
+  auto fin = [](double v) { return std::isfinite(v); };
+  if (!fin(p.eps) || !fin(p.xi) || !fin(p.zeta) || !fin(p.delta) || !fin(p.alpha0) || !fin(p.tol))
+    return false;
+  if (!(p.xi > 0 && p.xi < 1) || !(p.zeta > 0 && p.zeta < 1) || !(p.delta > 0) || p.eps < 0)
+    return false;
+  if (p.max_iter < 1 || p.check_every < 1 || p.ls_max_trials < 1 || p.tol < 0) return false;
+  if (p.linesearch != 0 && p.linesearch != 1) return false;
+  if (p.ls_norm != 2) return false;  // the GPU path implements the Euclidean test only
+  if (p.balance != EMD_BAL_NONE && p.balance != EMD_BAL_MEAN) return false;
+  if (p.tile < 0 || p.tile > kNumShapes) return false;
+  if (p.launch_mode < 0 || p.launch_mode > 1) return false;
+  return true;
+}
+
+int pick_shape(const emd_params &p, int B, const int *nt, const int *nr) {
+  if (p.tile > 0) return p.tile - 1;
+  int nr_max = 0;
+  for (int b = 0; b < B; ++b) nr_max = std::max(nr_max, nr[b]);
+  (void)nt;
+  if (nr_max == 1) return 5;  // 1 x 248: one receiver
+  if (nr_max <= 8) return 1;  // 8 x 120
+  return 0;                   // 16 x 120
+}
+
+bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+// With tol > 0 the host checks the finished-gather count after every kPoll passes.
+constexpr int kPoll = 64;
+
+// Enqueues fused passes on a stream: replays of one CUDA graph of kChunk passes,
+// captured once per solve, plus plain launches for the remainder (launch_mode 1: plain
+// launches only).
+class PassLauncher {
+ public:
+  static constexpr int kChunk = 32;
+  PassLauncher(const Shape &sh, const Ctl &ctl, int grid, size_t smem, int mode)
+      : sh_(sh), ctl_(ctl), grid_(grid), smem_(smem), mode_(mode) {}
+  ~PassLauncher() {
+    if (exec_) cudaGraphExecDestroy(exec_);
+    if (graph_) cudaGraphDestroy(graph_);
+  }
+  emd_status launch(int n, cudaStream_t stream) {
+    int done = 0;
+    if (mode_ == 0 && n >= kChunk) {
+      if (!exec_ && capture() != EMD_OK) return EMD_ERR_CUDA;
+      for (; done + kChunk <= n; done += kChunk) EMD_CK(cudaGraphLaunch(exec_, stream));
+    }
+    for (; done < n; ++done) sh_.iter<<<grid_, kThreads, smem_, stream>>>(ctl_);
+    EMD_CK(cudaGetLastError());
+    return EMD_OK;
+  }
+
+ private:
+  emd_status capture() {
+    cudaStream_t cs;
+    EMD_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      for (int i = 0; i < kChunk; ++i) sh_.iter<<<grid_, kThreads, smem_, cs>>>(ctl_);
+      ok = cudaStreamEndCapture(cs, &graph_) == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&exec_, graph_, 0) == cudaSuccess;
+    cudaStreamDestroy(cs);
+    if (!ok) {
+      (void)cudaGetLastError();
+      return EMD_ERR_CUDA;
+    }
+    return EMD_OK;
+  }
+  const Shape &sh_;
+  Ctl ctl_;
+  int grid_;
+  size_t smem_;
+  int mode_;
+  cudaGraph_t graph_ = nullptr;
+  cudaGraphExec_t exec_ = nullptr;
+};
+
+emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
+                      const int *nr, const double *dt, const double *dx, const emd_params *pp,
+                      float *const *phi, float *const *m, emd_result *results, void *ws,
+                      size_t ws_bytes, cudaStream_t stream) {
+  emd_params p;
+  emd_default_params(&p);
+  if (pp) p = *pp;
+  if (B < 1 || !f_obs || !f_pred || !nt || !nr || !dt || !dx || !phi || !m || !results)
+    return EMD_ERR_ARG;
+  if (!params_ok(p)) return EMD_ERR_ARG;
+  if (B > 1 && (p.phi_init || p.m_init)) return EMD_ERR_ARG;
+  for (int b = 0; b < B; ++b) {
+    if (!size_ok(nt[b], nr[b])) return EMD_ERR_ARG;
+    if (!f_obs[b] || !f_pred[b] || !phi[b] || !m[b]) return EMD_ERR_ARG;
+    if (!(dt[b] > 0) || !std::isfinite(dt[b]) || !(dx[b] > 0) || !std::isfinite(dx[b]))
+      return EMD_ERR_ARG;
+  }
+  const Layout L = layout(B, nt, nr);
+  if (!ws || !aligned256(ws) || ws_bytes < L.total) return EMD_ERR_WORKSPACE;
+
+  const int si = pick_shape(p, B, nt, nr);
+  const Shape &sh = kShapes[si];
+  char *base = static_cast<char *>(ws);
+
+  std::vector<Shot> shots(B);
+  std::vector<int> tile_shot;
+  int nr_max = 0;
+  for (int b = 0; b < B; ++b) {
+    Shot &S = shots[b];
+    std::memset(&S, 0, sizeof(S));
+    S.p_obs = f_obs[b];
+    S.p_pred = f_pred[b];
+    S.phi_out = phi[b];
+    S.m_out = m[b];
+    S.phi_init = p.phi_init;
+    S.m_init = p.m_init;
+    S.nt = nt[b];
+    S.nr = nr[b];
+    S.ntp = ntp_of(nt[b]);
+    S.plane = nr[b] * S.ntp;
+    const size_t pl = L.plane[b];
+    char *g = base + L.gather[b];
+    S.f = reinterpret_cast<float *>(g);
+    // u[m] spans two plane slots; its t plane is addressed as x plane + `plane` floats,
+    // which stays inside the pair because plane * 4 <= pl (and is 128-byte aligned).
+    for (int u = 0; u < 3; ++u) S.u[u] = reinterpret_cast<float *>(g + (1 + 2 * u) * pl);
+    S.ph[0] = reinterpret_cast<float *>(g + 7 * pl);
+    S.ph[1] = reinterpret_cast<float *>(g + 8 * pl);
+    S.tiles_j = (nt[b] + (sh.w - 8) - 1) / (sh.w - 8);
+    S.tile0 = static_cast<int>(tile_shot.size());
+    S.ntiles = tiles_of(sh, nt[b], nr[b]);
+    tile_shot.insert(tile_shot.end(), S.ntiles, b);
+    const bool one_d = nr[b] == 1;
+    S.rdx = one_d ? 0.0f : static_cast<float>(1.0 / dx[b]);
+    S.rdt = static_cast<float>(1.0 / dt[b]);
+    S.area = one_d ? dt[b] : dx[b] * dt[b];
+    S.lambda = 4.0 / (dt[b] * dt[b]) + (one_d ? 0.0 : 4.0 / (dx[b] * dx[b]));
+    nr_max = std::max(nr_max, nr[b]);
+  }
+  const int grid = static_cast<int>(tile_shot.size());
+
+  State *states = reinterpret_cast<State *>(base + L.states);
+  Shot *dshots = reinterpret_cast<Shot *>(base + L.shots);
+  int *dtiles = reinterpret_cast<int *>(base + L.tiles);
+  int *n_done = reinterpret_cast<int *>(base + L.misc);
+  double *acc = reinterpret_cast<double *>(base + L.acc);
+
+  EMD_CK(cudaMemcpyAsync(dshots, shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
+  EMD_CK(cudaMemcpyAsync(dtiles, tile_shot.data(), sizeof(int) * tile_shot.size(),
+                         cudaMemcpyHostToDevice, stream));
+  EMD_CK(cudaMemsetAsync(states, 0, sizeof(State) * B, stream));
+  EMD_CK(cudaMemsetAsync(n_done, 0, sizeof(int), stream));
+  EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double) * emd::kSpread * emd::kAcc * B, stream));
+
+  Ctl ctl{};
+  ctl.eps = p.eps;
+  ctl.xi = p.xi;
+  ctl.zeta = p.zeta;
+  ctl.delta = p.delta;
+  ctl.tol = p.tol;
+  ctl.alpha0 = p.alpha0;
+  ctl.max_iter = p.max_iter;
+  ctl.check_every = p.check_every;
+  ctl.ls_max_trials = p.ls_max_trials;
+  ctl.linesearch = p.linesearch;
+  ctl.balance = p.balance;
+  ctl.debug_fault = p.debug_fault;
+  ctl.shots = dshots;
+  ctl.states = states;
+  ctl.acc = acc;
+  ctl.tile_shot = dtiles;
+  ctl.n_done = n_done;
+
+  const size_t smem = smem_bytes(sh);
+  EMD_CK(cudaFuncSetAttribute(sh.iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(smem)));
+  EMD_CK(cudaFuncSetAttribute(sh.fin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(smem)));
+
+  emd::k_prepare<<<dim3(std::min(nr_max, 128), B), kThreads, 0, stream>>>(ctl);
+  EMD_CK(cudaGetLastError());
+
+  PassLauncher passes(sh, ctl, grid, smem, p.launch_mode);
+  if (p.tol <= 0.0) {
+    const emd_status s = passes.launch(p.max_iter, stream);
+    if (s != EMD_OK) return s;
+  } else {
+    // Run in blocks of `poll` passes and stop once every gather reports done.
+    const int poll = kPoll;
+    int launched = 0;
+    while (launched < p.max_iter) {
+      const int n = std::min(poll, p.max_iter - launched);
+      const emd_status s = passes.launch(n, stream);
+      if (s != EMD_OK) return s;
+      launched += n;
+      int h_done = 0;
+      EMD_CK(cudaMemcpyAsync(&h_done, n_done, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      EMD_CK(cudaStreamSynchronize(stream));
+      if (h_done >= B) break;
+    }
+  }
+
+  sh.fin<<<grid, kThreads, smem, stream>>>(ctl);
+  EMD_CK(cudaGetLastError());
+
+  std::vector<State> hs(B);
+  EMD_CK(cudaMemcpyAsync(hs.data(), states, sizeof(State) * B, cudaMemcpyDeviceToHost, stream));
+  EMD_CK(cudaStreamSynchronize(stream));
+
+  emd_status first = EMD_OK;
+  for (int b = 0; b < B; ++b) {
+    const State &st = hs[b];
+    emd_result &r = results[b];
+    const Shot &S = shots[b];
+    const double *g = st.gap_sums;  // final u and phi: sum|u|, sum u^2, <phi,f>, h* terms
+    r.dist = S.area * (g[0] + 0.5 * p.eps * g[1]);
+    r.dist_l1 = S.area * g[0];
+    r.mass_mu = st.mass_mu;
+    r.mass_nu = st.mass_nu;
+    r.imbalance = st.imbalance;
+    // residual of the last iteration from its sums (the last pass measured u^K against u^{K-1})
+    r.r_feas = st.fnorm > 0.0 ? std::sqrt(st.s_p2) / st.fnorm : std::sqrt(st.s_p2);
+    r.r_step = std::sqrt(st.s_du2) / std::max(std::sqrt(st.s_u2), 1e-30);
+    r.residual = std::max(r.r_feas, r.r_step);
+    r.duality_gap = p.eps > 0.0 ? S.area * (g[0] + 0.5 * p.eps * g[1] - g[2] + g[3] / (2.0 * p.eps))
+                                : std::nan("");
+    r.alpha = st.alpha;
+    r.theta = st.theta;
+    r.iters = st.k;
+    r.ls_trials = st.trials;
+    r.status = st.status;
+    if (first == EMD_OK && st.status != EMD_OK) first = static_cast<emd_status>(st.status);
+  }
+  return first;
+}
+
+}  // namespace
+
+extern "C" {
+
+void emd_default_params(emd_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps = 1e-4;
+  p->xi = 0.5;
+  p->zeta = 0.99;
+  p->delta = 1e5;
+  p->alpha0 = 0.0;
+  p->tol = 0.0;
+  p->max_iter = 2000;
+  p->check_every = 10;
+  p->ls_max_trials = 40;
+  p->linesearch = 1;
+  p->ls_norm = 2;
+  p->balance = EMD_BAL_MEAN;
+  p->phi_init = nullptr;
+  p->m_init = nullptr;
+  p->tile = 0;
+  p->launch_mode = 0;
+  p->debug_fault = 0;
+}
+
+int emd_tile_count(void) { return kNumShapes; }
+
+size_t emd_workspace_size(int nt, int nr) {
+  if (!size_ok(nt, nr)) return 0;
+  return layout(1, &nt, &nr).total;
+}
+
+size_t emd_batched_workspace_size(int B, const int *nt, const int *nr) {
+  if (B < 1 || !nt || !nr) return 0;
+  for (int b = 0; b < B; ++b)
+    if (!size_ok(nt[b], nr[b])) return 0;
+  return layout(B, nt, nr).total;
+}
+
+emd_status emd_dyn_solve(const float *f_obs, const float *f_pred, int nt, int nr, double dt,
+                         double dx, const emd_params *params, float *phi, float *m,
+                         emd_result *result, void *workspace, size_t ws_bytes,
+                         emd_stream_t stream) {
+  return solve_impl(1, &f_obs, &f_pred, &nt, &nr, &dt, &dx, params, &phi, &m, result, workspace,
+                    ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+emd_status emd_dyn_solve_batched(int B, const float *const *f_obs, const float *const *f_pred,
+                                 const int *nt, const int *nr, const double *dt,
+                                 const double *dx, const emd_params *params,
+                                 float *const *phi, float *const *m, emd_result *results,
+                                 void *workspace, size_t ws_bytes, emd_stream_t stream) {
+  return solve_impl(B, f_obs, f_pred, nt, nr, dt, dx, params, phi, m, results, workspace,
+                    ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+emd_status emd_decompose(const float *f_obs, const float *f_pred, int nt, int nr, double dt,
+                         double dx, float *mu, float *nu, double *masses, void *workspace,
+                         size_t ws_bytes, emd_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!f_obs || !f_pred || !size_ok(nt, nr)) return EMD_ERR_ARG;
+  if (!(dt > 0) || !std::isfinite(dt) || !(dx > 0) || !std::isfinite(dx)) return EMD_ERR_ARG;
+  const Layout L = layout(1, &nt, &nr);
+  if (!workspace || !aligned256(workspace) || ws_bytes < L.total) return EMD_ERR_WORKSPACE;
+  double *acc = reinterpret_cast<double *>(static_cast<char *>(workspace) + L.misc + 64);
+  const size_t n = static_cast<size_t>(nt) * nr;
+  EMD_CK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), stream));
+  const int blocks = static_cast<int>(std::min<size_t>((n + kThreads - 1) / kThreads, 2048));
+  emd::k_decompose<<<blocks, kThreads, 0, stream>>>(f_obs, f_pred, n, mu, nu, acc);
+  EMD_CK(cudaGetLastError());
+  if (masses) {
+    double h[2];
+    EMD_CK(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    EMD_CK(cudaStreamSynchronize(stream));
+    const double area = nr == 1 ? dt : dx * dt;
+    masses[0] = area * h[0];
+    masses[1] = area * h[1];
+  }
+  return EMD_OK;
+}
+
+emd_status emd_adjoint(const float *phi, int nt, int nr, double dt, double dx, int balance,
+                       const float *grad_out, float *grad_pred, float *grad_obs,
+                       void *workspace, size_t ws_bytes, emd_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!phi || !grad_pred || !size_ok(nt, nr)) return EMD_ERR_ARG;
+  if (balance != EMD_BAL_NONE && balance != EMD_BAL_MEAN) return EMD_ERR_ARG;
+  if (!(dt > 0) || !std::isfinite(dt) || !(dx > 0) || !std::isfinite(dx)) return EMD_ERR_ARG;
+  const Layout L = layout(1, &nt, &nr);
+  if (!workspace || !aligned256(workspace) || ws_bytes < L.total) return EMD_ERR_WORKSPACE;
+  double *acc = reinterpret_cast<double *>(static_cast<char *>(workspace) + L.misc + 128);
+  const size_t n = static_cast<size_t>(nt) * nr;
+  const int blocks = static_cast<int>(std::min<size_t>((n + kThreads - 1) / kThreads, 2048));
+  const double area = nr == 1 ? dt : dx * dt;
+  if (balance == EMD_BAL_MEAN) {
+    EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double), stream));
+    emd::k_adj_sum<<<blocks, kThreads, 0, stream>>>(phi, n, acc);
+    EMD_CK(cudaGetLastError());
+  }
+  emd::k_adj_scale<<<blocks, kThreads, 0, stream>>>(phi, n, area, balance, acc, grad_out,
+                                                     grad_pred, grad_obs);
+  EMD_CK(cudaGetLastError());
+  return EMD_OK;
+}
+
+const char *emd_status_string(emd_status s) {
+  switch (s) {
+    case EMD_OK: return "ok";
+    case EMD_ERR_ARG: return "invalid argument";
+    case EMD_ERR_CUDA: return "CUDA error";
+    case EMD_ERR_NONFINITE: return "non-finite iterate";
+    case EMD_ERR_LINESEARCH: return "linesearch did not terminate";
+    case EMD_ERR_TIMEOUT: return "device wait timed out";
+    case EMD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

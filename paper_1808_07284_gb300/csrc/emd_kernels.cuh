@@ -1,0 +1,602 @@
+// Device code of the GB300 dynamic-formulation EMD solver (PDHG with linesearch).
+//
+// One PDHG iteration of Algorithm 1 is ONE fused stencil pass over the gather.  Pass k:
+//   (1) finishes iteration k-1's dual ascent (Sec. 2.2, dual update):
+//         phi^k = phi^{k-1} + c_k (p_{k-1} + theta_k q_{k-1}),  c_k = delta alpha_k,
+//       where p_{k-1} = div u^k + f and q_{k-1} = div(u^k - u^{k-1}), so that
+//       div ubar + f = p + theta q with ubar = u^k + theta (u^k - u^{k-1});
+//   (2) takes iteration k's primal prox (Sec. 2.2, primal update):
+//         u^{k+1} = shrink(u^k + alpha_k grad phi^k, alpha_k) / (1 + eps alpha_k);
+//   (3) accumulates the inner products the linesearch of iteration k needs.  With the
+//       Euclidean norm, a trial step a gives dphi(a) = delta a (p_k + s q_k), s = a/alpha_k,
+//       so the test  sqrt(delta) a ||grad dphi|| <= zeta ||dphi||  reads
+//         delta a^2 (G_pp + 2 s G_pq + s^2 G_qq) <= zeta^2 (P_pp + 2 s P_pq + s^2 P_qq)
+//       with six sums that do not depend on a.  One pass therefore settles every
+//       backtracking trial of Algorithm 1 exactly; the trial loop runs on scalars.
+//       The same pass sums the stopping residual and the distance of u^{k+1}.
+// The last CTA of each gather (atomic ticket) reduces the FP64 accumulators and takes
+// the linesearch decision, writing (alpha_{k+1}, theta_{k+1}, c_{k+1}) for pass k+1.
+//
+// Tiles: TI rows (receivers) x TJ = W - 8 columns (time) per CTA, staged in shared
+// memory with a 2-row / 4-column halo on every side (the dependency cone of the three
+// fused steps), loaded with 16-byte cp.async and zero fill outside the pitched planes.
+// Iterates are FP32; per-thread partial sums are FP32 over a handful of cells and
+// one warp, everything above a warp is FP64 (FP64 atomics into L2).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace emd {
+
+constexpr int kThreads = 256;
+constexpr int kAcc = 12;  // FP64 accumulators per gather
+
+// Per-gather constants of one solve (device copy in the workspace).
+struct Shot {
+  const float *p_obs, *p_pred;      // caller inputs [nr][nt]
+  float *phi_out, *m_out;           // caller outputs [nr][nt], [2][nr][nt]
+  const float *phi_init, *m_init;   // optional warm start (caller, may be null)
+  float *f;                         // Pcal - Pobs, pitched [nr][ntp]
+  float *u[3];                      // u^m lives in u[m % 3]: x plane then t plane, pitched
+  float *ph[2];                     // phi^m lives in ph[m & 1], pitched
+  int nt, nr, ntp, tiles_j;         // ntp: row pitch in floats (multiple of 32)
+  int tile0, ntiles;                // first global tile index and tile count of this gather
+  int plane;                        // nr * ntp
+  float rdx, rdt;                   // 1/dx (0 when nr == 1), 1/dt
+  double area, lambda;              // dx*dt (dt when nr == 1); 4/dx^2 + 4/dt^2
+};
+
+// Per-gather solver state, written by the deciding CTA of each pass.  The first 32
+// bytes are what every CTA of the next pass needs (one vector load).
+struct alignas(16) State {
+  int k, done;                      // accepted iterations so far; 1 once stopped
+  float alpha_f, coef_f, theta_f;   // FP32 copies of alpha_k, c_k, theta_k
+  float inv_f, fmean_f;             // 1 / (1 + eps alpha_k), the removed mean of f
+  int status;
+  double alpha, theta, coef;        // alpha_k, theta_k, c_k (FP64, the decision's copies)
+  double beta_fixed;                // fixed-step dual step (linesearch == 0)
+  double fmean, fnorm;              // mean of f removed by balancing, ||f - fmean||
+  double s_p2, s_u1, s_u2, s_du2;   // last pass: ||p||^2, sum|u|, sum u^2, ||du||^2
+  double r_feas, r_step;            // residual at the last stopping test
+  double gap_sums[4];               // final pass: sum|u|, sum u^2, <phi,f>, sum (|grad phi|-1)_+^2
+  double mass_mu, mass_nu, imbalance;
+  int trials;
+  unsigned int ticket;
+};
+
+constexpr int kSpread = 32;         // copies of each accumulator (spreads the atomics)
+// Solve-wide parameters, passed by value to every kernel.
+struct Ctl {
+  double eps, xi, zeta, delta, tol, alpha0;
+  int max_iter, check_every, ls_max_trials, linesearch, balance, debug_fault;
+  const Shot *shots;
+  State *states;
+  double *acc;                      // [gather][kSpread][kAcc] FP64 accumulators (zeroed)
+  const int *tile_shot;             // global tile -> gather
+  int *n_done;                      // gathers finished
+};
+
+enum { ST_OK = 0, ST_NONFINITE = 3, ST_LINESEARCH = 4 };
+
+// ------------------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool ok) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int sz = ok ? 16 : 0;  // src-size 0 fills the 16 bytes with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// shrink(x, y) = (1 - y/|x|) x for |x| >= y, else 0  ==  sign(x) max(|x| - y, 0).
+__device__ __forceinline__ float shrinkf(float v, float a) {
+  const float av = fabsf(v);
+  return av >= a ? copysignf(av - a, v) : 0.0f;
+}
+
+// Reduce N per-thread FP32 partials of a CTA: FP32 within the warp, FP64 across warps,
+// then one FP64 atomic add per value into acc[0..N).  Every thread must call it.
+template <int N>
+__device__ __forceinline__ void block_accumulate(float (&v)[N], double *acc) {
+  // acc points at this CTA's copy: acc[0..N)
+  __shared__ float part[kThreads / 32][N];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    const float w = warp_sum(v[n]);
+    if (lane == 0) part[warp][n] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += static_cast<double>(part[w][threadIdx.x]);
+    atomicAdd(acc + threadIdx.x, s);
+  }
+}
+
+// Returns true in the one CTA of a gather that finished last (all threads see it).
+// Each CTA's atomics above are made visible before it takes its ticket.
+__device__ __forceinline__ bool last_block(unsigned int *ticket, int nblocks) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == static_cast<unsigned>(nblocks - 1));
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// In the deciding CTA: sums the kSpread copies of the first N accumulators of a gather
+// (warp w takes values w, w + 8, ...), zeroes them for the next pass, and leaves the
+// totals in out[0..N).  Every thread must call it.
+template <int N>
+__device__ __forceinline__ void gather_totals(double *acc, double (&out)[N]) {
+  __shared__ double tot[N];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  static_assert(kSpread == 32, "one lane per copy");
+  for (int n = warp; n < N; n += kThreads / 32) {
+    double *a = acc + lane * kAcc + n;
+    double v = __ldcg(a);
+    *a = 0.0;
+    v = warp_sum_d(v);
+    if (lane == 0) tot[n] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int n = 0; n < N; ++n) out[n] = tot[n];
+}
+
+// ------------------------------------------------------------------------------ decision
+
+// Writes the FP32 copies of the step sizes that the next pass reads.
+__device__ __forceinline__ void publish(State *st, double eps) {
+  st->alpha_f = static_cast<float>(st->alpha);
+  st->coef_f = static_cast<float>(st->coef);
+  st->theta_f = static_cast<float>(st->theta);
+  st->inv_f = 1.0f / (1.0f + static_cast<float>(eps * st->alpha));
+}
+
+// Linesearch decision of Algorithm 1 from the sums of pass k (one thread).
+// a: 0 P_pp, 1 P_pq, 2 P_qq, 3 G_pp, 4 G_pq, 5 G_qq, 6 sum|u|, 7 sum u^2, 8 sum du^2.
+// Trial t uses a = alpha_k s, s = sqrt(1 + theta_k) xi^(t-1), so no division is needed.
+__device__ void decide(const Ctl &c, State *st, const double (&a_)[9]) {
+  const double Ppp = a_[0], Ppq = a_[1], Pqq = a_[2], Gpp = a_[3], Gpq = a_[4], Gqq = a_[5];
+  double fin = 0.0;
+#pragma unroll
+  for (int n = 0; n < 9; ++n) fin += a_[n];
+  st->s_p2 = Ppp;
+  st->s_u1 = a_[6];
+  st->s_u2 = a_[7];
+  st->s_du2 = a_[8];
+  bool done = false;
+  if (!isfinite(fin)) {
+    st->status = ST_NONFINITE;
+    done = true;
+  } else if (c.linesearch) {
+    const double ak = st->alpha;
+    double s = sqrt(1.0 + st->theta);  // upper end of [alpha_k, alpha_k sqrt(1+theta_k)]
+    int t = 1;
+    bool ok = false;
+    for (; t <= c.ls_max_trials; ++t) {
+      const double a = ak * s;
+      const double lhs = c.delta * a * a * (Gpp + s * (2.0 * Gpq + s * Gqq));
+      const double rhs = c.zeta * c.zeta * (Ppp + s * (2.0 * Ppq + s * Pqq));
+      if (lhs <= rhs && c.debug_fault != 1) {
+        ok = true;
+        break;
+      }
+      s *= c.xi;
+    }
+    if (ok) {
+      st->theta = s;
+      st->alpha = ak * s;
+      st->coef = c.delta * st->alpha;
+      st->trials += t;
+      st->k += 1;
+      publish(st, c.eps);
+    } else {
+      st->trials += c.ls_max_trials;
+      st->status = ST_LINESEARCH;
+      done = true;
+    }
+  } else {
+    st->coef = st->beta_fixed;
+    st->theta = 1.0;
+    st->trials += 1;
+    st->k += 1;
+    publish(st, c.eps);
+  }
+  const int k = st->k;
+  if (!done && k >= c.max_iter) done = true;
+  if (!done && c.tol > 0.0 && k % c.check_every == 0) {
+    const double fnorm = st->fnorm;
+    const double r_feas = fnorm > 0.0 ? sqrt(Ppp) / fnorm : sqrt(Ppp);
+    const double r_step = sqrt(a_[8]) / fmax(sqrt(a_[7]), 1e-30);
+    st->r_feas = r_feas;
+    st->r_step = r_step;
+    if (fmax(r_feas, r_step) <= c.tol) done = true;
+  }
+  if (done) {
+    st->done = 1;
+    atomicAdd(c.n_done, 1);
+  }
+}
+
+// ------------------------------------------------------------------------------ prepare
+
+// Builds f = Pcal - Pobs in the pitched plane, zeroes or warm-starts the iterates, sums
+// f, f^2, mu, nu and the exact (FP64) differences in FP64 (Sec. 2.1 mass balance) and
+// initialises each gather's state.  Grid: (PX, B); CTA x walks rows x, x + PX, ... of
+// gather blockIdx.y.
+__global__ void __launch_bounds__(kThreads) k_prepare(Ctl c) {
+  const int b = blockIdx.y;
+  const Shot S = c.shots[b];
+  State *st = c.states + b;
+  double sf = 0.0, sf2 = 0.0, smu = 0.0, snu = 0.0, sdx = 0.0;
+  for (int i = blockIdx.x; i < S.nr; i += gridDim.x) {
+    for (int j = threadIdx.x; j < S.ntp; j += kThreads) {
+      const bool in = j < S.nt;
+      const size_t g = static_cast<size_t>(i) * S.nt + j;
+      const int o = i * S.ntp + j;
+      const float po = in ? S.p_obs[g] : 0.0f;
+      const float pp = in ? S.p_pred[g] : 0.0f;
+      const float f = pp - po;
+      S.f[o] = f;
+      const double fd = static_cast<double>(f);
+      sf += fd;
+      sf2 += fd * fd;
+      sdx += static_cast<double>(pp) - static_cast<double>(po);
+      smu += static_cast<double>(fmaxf(pp, 0.0f)) + static_cast<double>(fmaxf(-po, 0.0f));
+      snu += static_cast<double>(fmaxf(po, 0.0f)) + static_cast<double>(fmaxf(-pp, 0.0f));
+      float ux = 0.0f, ut = 0.0f, ph = 0.0f;
+      if (in && S.m_init) {
+        // the outer faces (x plane row 0, t plane column 0) carry no flux
+        ux = i > 0 ? S.m_init[g] : 0.0f;
+        ut = j > 0 ? S.m_init[static_cast<size_t>(S.nr) * S.nt + g] : 0.0f;
+      }
+      if (in && S.phi_init) ph = S.phi_init[g];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        S.u[m][o] = m == 0 ? ux : 0.0f;
+        S.u[m][S.plane + o] = m == 0 ? ut : 0.0f;
+      }
+      S.ph[0][o] = 0.0f;
+      S.ph[1][o] = ph;  // pass 0 reads phi^{-1} := phi_init from ph[1]
+    }
+  }
+  // block reduction in FP64 (this kernel runs once per solve)
+  __shared__ double red[kThreads / 32][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[5] = {sf, sf2, smu, snu, sdx};
+#pragma unroll
+  for (int n = 0; n < 5; ++n) {
+    v[n] = warp_sum_d(v[n]);
+    if (lane == 0) red[warp][n] = v[n];
+  }
+  __syncthreads();
+  double *acc = c.acc + static_cast<size_t>(b) * kSpread * kAcc;
+  if (threadIdx.x < 5) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
+    atomicAdd(acc + (blockIdx.x % kSpread) * kAcc + threadIdx.x, t);
+  }
+  if (!last_block(&st->ticket, gridDim.x)) return;
+  double a_[5];
+  gather_totals<5>(acc, a_);
+  if (threadIdx.x != 0) return;
+  const double N = static_cast<double>(S.nr) * S.nt;
+  const double fmean = c.balance ? a_[0] / N : 0.0;
+  st->fmean = fmean;
+  st->fmean_f = static_cast<float>(fmean);
+  st->fnorm = sqrt(fmax(a_[1] - 2.0 * fmean * a_[0] + N * fmean * fmean, 0.0));
+  st->mass_mu = S.area * a_[2];
+  st->mass_nu = S.area * a_[3];
+  st->imbalance = S.area * a_[4];
+  double alpha;
+  if (c.linesearch) {
+    alpha = c.alpha0 > 0.0 ? c.alpha0 : 1.0 / sqrt(c.delta * S.lambda);
+  } else {
+    alpha = c.alpha0 > 0.0 ? c.alpha0 : 1.0 / sqrt(S.lambda);
+  }
+  st->alpha = alpha;
+  st->beta_fixed = 1.0 / (S.lambda * alpha);
+  st->theta = 1.0;
+  st->coef = 0.0;  // pass 0: phi^0 = phi^{-1} (the initial potential)
+  publish(st, c.eps);
+  st->k = 0;
+  st->trials = 0;
+  st->status = ST_OK;
+  st->r_feas = st->r_step = -1.0;
+  st->ticket = 0u;
+  __threadfence();
+  st->done = 0;
+}
+
+// ------------------------------------------------------------------------------ the pass
+
+// FINAL = false: PDHG pass k (see the file header).  FINAL = true: after the last
+// accepted iteration K, finishes phi^K, writes phi^K and u^K to the caller's outputs and
+// sums the duality gap.  Grid: one CTA per tile of every gather (tile_shot maps it).
+template <int TI, int W, bool FINAL>
+__global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
+  constexpr int TJ = W - 8;          // output columns per tile
+  constexpr int R = TI + 4;          // staged rows: i0-2 .. i0+TI+1
+  constexpr int NRS = kThreads / W;  // rows per sweep of the CTA
+  static_assert(kThreads % W == 0, "W must divide the CTA");
+  extern __shared__ float4 smem4[];
+  float *sm = reinterpret_cast<float *>(smem4);
+  float *UAx = sm;          // u^{k-1} (then u^{k+1})
+  float *UAt = sm + 1 * R * W;
+  float *UBx = sm + 2 * R * W;  // u^k
+  float *UBt = sm + 3 * R * W;
+  float *PH = sm + 4 * R * W;   // phi^{k-1} -> phi^k -> q_k
+  float *FF = sm + 5 * R * W;   // f -> p_k
+
+  const int gtile = blockIdx.x;
+  const int s = c.tile_shot[gtile];
+  const Shot &S = c.shots[s];
+  State *st = c.states + s;
+
+  // the 32 hot bytes of the state: k, done and the FP32 step sizes
+  const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(st));
+  const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(st) + 1);
+  if (!FINAL && h0.y) return;  // this gather has stopped
+  const int k = h0.x;
+  const float alpha = __int_as_float(h0.z), coef = __int_as_float(h0.w);
+  const float theta = __int_as_float(h1.x), inv = __int_as_float(h1.y);
+  const float fmean = __int_as_float(h1.z);
+
+  const int nr = S.nr, nt = S.nt, ntp = S.ntp, plane = S.plane;
+  const float rdx = S.rdx, rdt = S.rdt;
+  const int lt = gtile - S.tile0;
+  const int i0 = (lt / S.tiles_j) * TI;
+  const int j0 = (lt % S.tiles_j) * TJ;
+
+  const float *u_prev = S.u[k == 0 ? 0 : (k - 1) % 3];
+  const float *u_cur = S.u[k % 3];
+  float *u_next = S.u[(k + 1) % 3];
+  const float *ph_prev = S.ph[(k + 1) & 1];
+  float *ph_cur = S.ph[k & 1];
+
+  // ---- stage the six input planes (rows i0-2.., columns j0-4..) into shared memory
+  {
+    const float *src[6] = {u_prev, u_prev + plane, u_cur, u_cur + plane, ph_prev, S.f};
+    constexpr int Q = W / 4;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      for (int v = threadIdx.x; v < R * Q; v += kThreads) {
+        const int r = v / Q, q = v - r * Q;
+        const int gi = i0 - 2 + r, gj = j0 - 4 + 4 * q;
+        const bool ok = gi >= 0 && gi < nr && gj >= 0 && gj < ntp;
+        const float *g = ok ? src[a] + gi * ntp + gj : src[a];
+        cp_async16(sm + a * R * W + r * W + 4 * q, g, ok);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+
+  const int tx = threadIdx.x % W, ty = threadIdx.x / W;
+  const int c_ = tx;             // shared-memory column of this thread
+  const int gj = j0 - 4 + c_;    // its global time index
+  const bool col_in = gj >= 0 && gj < nt;
+
+  // ---- phase 1: phi^k on rows i0-2..i0+TI, columns j0-2..j0+TJ
+  if (c_ >= 2 && c_ < TJ + 5) {
+    for (int r = ty; r < TI + 3; r += NRS) {
+      const int gi = i0 - 2 + r;
+      const int o = r * W + c_;
+      float phk = 0.0f;
+      if (col_in && gi >= 0 && gi < nr) {
+        const bool xl = gi > 0, xr = gi + 1 < nr, tl = gj > 0, tr = gj + 1 < nt;
+        const float bxl = xl ? UBx[o] : 0.0f, bxr = xr ? UBx[o + W] : 0.0f;
+        const float btl = tl ? UBt[o] : 0.0f, btr = tr ? UBt[o + 1] : 0.0f;
+        const float axl = xl ? UAx[o] : 0.0f, axr = xr ? UAx[o + W] : 0.0f;
+        const float atl = tl ? UAt[o] : 0.0f, atr = tr ? UAt[o + 1] : 0.0f;
+        const float divB = (bxr - bxl) * rdx + (btr - btl) * rdt;
+        const float divA = (axr - axl) * rdx + (atr - atl) * rdt;
+        const float p = divB + (FF[o] - fmean);
+        const float q = divB - divA;
+        phk = PH[o] + coef * (p + theta * q);
+        if (r >= 2 && r < TI + 2 && c_ >= 4 && c_ < TJ + 4) {
+          if (FINAL)
+            S.phi_out[static_cast<size_t>(gi) * nt + gj] = phk;
+          else
+            ph_cur[gi * ntp + gj] = phk;
+        }
+      }
+      PH[o] = phk;
+    }
+  }
+  __syncthreads();
+
+  if (FINAL) {
+    // ---- duality gap terms and the caller's copies of phi^K and u^K, over the tile
+    float v[4] = {0.f, 0.f, 0.f, 0.f};  // sum|u|, sum u^2, <phi, f>, sum (|grad phi|-1)_+^2
+    if (col_in && c_ >= 4 && c_ < TJ + 4) {
+      for (int r = 2 + ty; r < TI + 2; r += NRS) {
+        const int gi = i0 - 2 + r;
+        if (gi >= nr) break;
+        const int o = r * W + c_;
+        const float gx = gi > 0 ? (PH[o] - PH[o - W]) * rdx : 0.0f;
+        const float gt = gj > 0 ? (PH[o] - PH[o - 1]) * rdt : 0.0f;
+        const float ux = UBx[o], ut = UBt[o];
+        const size_t g = static_cast<size_t>(gi) * nt + gj;
+        S.m_out[g] = ux;
+        S.m_out[static_cast<size_t>(nr) * nt + g] = ut;
+        v[0] += fabsf(ux) + fabsf(ut);
+        v[1] += ux * ux + ut * ut;
+        v[2] += PH[o] * (FF[o] - fmean);
+        const float ex = fmaxf(fabsf(gx) - 1.0f, 0.0f), et = fmaxf(fabsf(gt) - 1.0f, 0.0f);
+        v[3] += ex * ex + et * et;
+      }
+    }
+    double *acc = c.acc + static_cast<size_t>(s) * kSpread * kAcc;
+    block_accumulate<4>(v, acc + (lt % kSpread) * kAcc);
+    if (!last_block(&st->ticket, S.ntiles)) return;
+    double a_[4];
+    gather_totals<4>(acc, a_);
+    if (threadIdx.x == 0) {
+      for (int n = 0; n < 4; ++n) st->gap_sums[n] = a_[n];
+      st->ticket = 0u;
+    }
+    return;
+  }
+
+  // ---- phase 2: u^{k+1} = prox on rows i0-1..i0+TI, columns j0-1..j0+TJ
+  if (c_ >= 3 && c_ < TJ + 5) {
+    for (int r = 1 + ty; r < TI + 3; r += NRS) {
+      const int gi = i0 - 2 + r;
+      const int o = r * W + c_;
+      float nx = 0.0f, nt_ = 0.0f;
+      if (col_in && gi >= 0 && gi < nr) {
+        const float gx = gi > 0 ? (PH[o] - PH[o - W]) * rdx : 0.0f;
+        const float gt = gj > 0 ? (PH[o] - PH[o - 1]) * rdt : 0.0f;
+        nx = shrinkf(UBx[o] + alpha * gx, alpha) * inv;
+        nt_ = shrinkf(UBt[o] + alpha * gt, alpha) * inv;
+        if (r >= 2 && r < TI + 2 && c_ >= 4 && c_ < TJ + 4) {
+          u_next[gi * ntp + gj] = nx;
+          u_next[plane + gi * ntp + gj] = nt_;
+        }
+      }
+      UAx[o] = nx;
+      UAt[o] = nt_;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 3: p_k = div u^{k+1} + f, q_k = div(u^{k+1} - u^k) on rows i0-1..i0+TI-1,
+  //      columns j0-1..j0+TJ-1 (p overwrites f, q overwrites phi^k)
+  if (c_ >= 3 && c_ < TJ + 4) {
+    for (int r = 1 + ty; r < TI + 2; r += NRS) {
+      const int gi = i0 - 2 + r;
+      const int o = r * W + c_;
+      float p = 0.0f, q = 0.0f;
+      if (col_in && gi >= 0 && gi < nr) {
+        const bool xl = gi > 0, xr = gi + 1 < nr, tl = gj > 0, tr = gj + 1 < nt;
+        const float nxl = xl ? UAx[o] : 0.0f, nxr = xr ? UAx[o + W] : 0.0f;
+        const float ntl = tl ? UAt[o] : 0.0f, ntr = tr ? UAt[o + 1] : 0.0f;
+        const float bxl = xl ? UBx[o] : 0.0f, bxr = xr ? UBx[o + W] : 0.0f;
+        const float btl = tl ? UBt[o] : 0.0f, btr = tr ? UBt[o + 1] : 0.0f;
+        const float divN = (nxr - nxl) * rdx + (ntr - ntl) * rdt;
+        const float divB = (bxr - bxl) * rdx + (btr - btl) * rdt;
+        p = divN + (FF[o] - fmean);
+        q = divN - divB;
+      }
+      FF[o] = p;
+      PH[o] = q;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 4: the linesearch / residual / distance sums over the tile
+  float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (col_in && c_ >= 4 && c_ < TJ + 4) {
+    for (int r = 2 + ty; r < TI + 2; r += NRS) {
+      const int gi = i0 - 2 + r;
+      if (gi >= nr) break;
+      const int o = r * W + c_;
+      const float p = FF[o], q = PH[o];
+      const float gpx = gi > 0 ? (p - FF[o - W]) * rdx : 0.0f;
+      const float gpt = gj > 0 ? (p - FF[o - 1]) * rdt : 0.0f;
+      const float gqx = gi > 0 ? (q - PH[o - W]) * rdx : 0.0f;
+      const float gqt = gj > 0 ? (q - PH[o - 1]) * rdt : 0.0f;
+      v[0] += p * p;
+      v[1] += p * q;
+      v[2] += q * q;
+      v[3] += gpx * gpx + gpt * gpt;
+      v[4] += gpx * gqx + gpt * gqt;
+      v[5] += gqx * gqx + gqt * gqt;
+      const float nx = UAx[o], nt_ = UAt[o];
+      const float dx_ = nx - UBx[o], dt_ = nt_ - UBt[o];
+      v[6] += fabsf(nx) + fabsf(nt_);
+      v[7] += nx * nx + nt_ * nt_;
+      v[8] += dx_ * dx_ + dt_ * dt_;
+    }
+  }
+  double *acc = c.acc + static_cast<size_t>(s) * kSpread * kAcc;
+  block_accumulate<9>(v, acc + (lt % kSpread) * kAcc);
+  if (!last_block(&st->ticket, S.ntiles)) return;
+  double a_[9];
+  gather_totals<9>(acc, a_);
+  if (threadIdx.x == 0) {
+    decide(c, st, a_);
+    st->ticket = 0u;
+  }
+}
+
+// ------------------------------------------------------------------------------ adjoint
+
+// Sum of phi in FP64 (per-thread FP32 over a grid-stride, FP64 above a warp).
+__global__ void __launch_bounds__(kThreads) k_adj_sum(const float *phi, size_t n, double *acc) {
+  float v[1] = {0.0f};
+  for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * kThreads)
+    v[0] += phi[i];
+  block_accumulate<1>(v, acc);
+}
+
+// grad_pred = g * area * (phi - mean), grad_obs = -grad_pred (Sec. 2.3 adjoint source).
+__global__ void __launch_bounds__(kThreads) k_adj_scale(const float *phi, size_t n, double area,
+                                                        int balance, const double *acc,
+                                                        const float *grad_out, float *gp,
+                                                        float *go) {
+  const float mean = balance ? static_cast<float>(acc[0] / static_cast<double>(n)) : 0.0f;
+  const float g = static_cast<float>((grad_out ? static_cast<double>(*grad_out) : 1.0) * area);
+  for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * kThreads) {
+    const float v = g * (phi[i] - mean);
+    gp[i] = v;
+    if (go) go[i] = -v;
+  }
+}
+
+// ------------------------------------------------------------------------------ decompose
+
+// mu = Pcal+ + Pobs-, nu = Pobs+ + Pcal- (Sec. 2.1) and their FP64 sums.
+__global__ void __launch_bounds__(kThreads) k_decompose(const float *po, const float *pp, size_t n,
+                                                        float *mu, float *nu, double *acc) {
+  double smu = 0.0, snu = 0.0;
+  for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * kThreads) {
+    const float o = po[i], p = pp[i];
+    const float m = fmaxf(p, 0.0f) + fmaxf(-o, 0.0f);
+    const float v = fmaxf(o, 0.0f) + fmaxf(-p, 0.0f);
+    if (mu) mu[i] = m;
+    if (nu) nu[i] = v;
+    smu += static_cast<double>(fmaxf(p, 0.0f)) + static_cast<double>(fmaxf(-o, 0.0f));
+    snu += static_cast<double>(fmaxf(o, 0.0f)) + static_cast<double>(fmaxf(-p, 0.0f));
+  }
+  __shared__ double red[kThreads / 32][2];
+  smu = warp_sum_d(smu);
+  snu = warp_sum_d(snu);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = smu;
+    red[threadIdx.x >> 5][1] = snu;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+    atomicAdd(acc + threadIdx.x, s);
+  }
+}
+
+}  // namespace emd

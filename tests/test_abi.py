@@ -1,0 +1,120 @@
+"""The C-ABI library loads, exports every symbol the header declares, agrees with the
+ctypes mirrors on struct layout, and validates arguments (host-only calls; no GPU)."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "emd_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1808_07284_gb300 import build
+    build.build()
+    import paper_1808_07284_gb300._binding as B
+    B.lib()
+    return B
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(emd_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(B):
+    names = _declared()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(B.lib(), n), n
+    assert set(names) == set(B.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}$", out, flags=re.M), n
+
+
+def test_struct_layout_matches_header(B, tmp_path):
+    """Compile a probe against the header with gcc and compare sizes and offsets."""
+    probe = tmp_path / "probe.c"
+    fields_p = [f for f, _ in B.EmdParams._fields_]
+    fields_r = [f for f, _ in B.EmdResult._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "emd_gb300.h"', "int main(void){"]
+    lines.append('printf("%zu %zu\\n", sizeof(emd_params), sizeof(emd_result));')
+    for f in fields_p:
+        lines.append(f'printf("p {f} %zu\\n", offsetof(emd_params, {f}));')
+    for f in fields_r:
+        lines.append(f'printf("r {f} %zu\\n", offsetof(emd_result, {f}));')
+    lines.append("return 0;}")
+    probe.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(probe), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    sp, sr = map(int, out[0].split())
+    assert sp == ctypes.sizeof(B.EmdParams) and sr == ctypes.sizeof(B.EmdResult)
+    for line in out[1:]:
+        if not line:
+            continue
+        kind, name, off = line.split()
+        cls = B.EmdParams if kind == "p" else B.EmdResult
+        assert getattr(cls, name).offset == int(off), name
+
+
+def test_defaults_are_the_papers_constants(B):
+    p = B.emd_default_params()
+    assert (p.eps, p.xi, p.zeta, p.delta) == (1e-4, 0.5, 0.99, 1e5)
+    assert p.max_iter == 2000 and p.linesearch == 1 and p.ls_norm == 2 and p.balance == B.EMD_BAL_MEAN
+    assert p.tol == 0.0 and p.check_every == 10 and p.ls_max_trials == 40
+    assert B.emd_tile_count() >= 1
+
+
+def test_workspace_size(B):
+    n = B.emd_workspace_size(3000, 400)
+    assert n >= 36 * 3000 * 400
+    assert B.emd_workspace_size(1, 5) == 0 and B.emd_workspace_size(5, 0) == 0
+    nb = B.emd_batched_workspace_size([100, 200], [3, 4])
+    assert nb >= B.emd_workspace_size(100, 3) + 36 * 200 * 4 - 4096
+
+
+def test_argument_errors_need_no_gpu(B):
+    """Invalid arguments come back as EMD_ERR_ARG / EMD_ERR_WORKSPACE before any CUDA call."""
+    L = B.lib()
+    res = B.EmdResult()
+    p = B.emd_default_params()
+    fake = ctypes.c_void_p(256)
+    # nt < 2
+    assert L.emd_dyn_solve(fake, fake, 1, 4, 1e-3, 10.0, ctypes.byref(p), fake, fake, ctypes.byref(res),
+                           fake, 1 << 20, None) == B.EMD_ERR_ARG
+    # dt <= 0
+    assert L.emd_dyn_solve(fake, fake, 8, 4, 0.0, 10.0, ctypes.byref(p), fake, fake, ctypes.byref(res),
+                           fake, 1 << 20, None) == B.EMD_ERR_ARG
+    # null input
+    assert L.emd_dyn_solve(None, fake, 8, 4, 1e-3, 10.0, ctypes.byref(p), fake, fake, ctypes.byref(res),
+                           fake, 1 << 20, None) == B.EMD_ERR_ARG
+    for bad in [dict(xi=1.0), dict(zeta=0.0), dict(delta=-1.0), dict(eps=-1e-4), dict(max_iter=0),
+                dict(ls_norm=1), dict(balance=7), dict(tile=99), dict(linesearch=2)]:
+        q = B.emd_default_params(**bad)
+        assert L.emd_dyn_solve(fake, fake, 8, 4, 1e-3, 10.0, ctypes.byref(q), fake, fake,
+                               ctypes.byref(res), fake, 1 << 20, None) == B.EMD_ERR_ARG, bad
+    # workspace too small / misaligned
+    assert L.emd_dyn_solve(fake, fake, 8, 4, 1e-3, 10.0, ctypes.byref(p), fake, fake, ctypes.byref(res),
+                           fake, 16, None) == B.EMD_ERR_WORKSPACE
+    assert L.emd_dyn_solve(fake, fake, 8, 4, 1e-3, 10.0, ctypes.byref(p), fake, fake, ctypes.byref(res),
+                           ctypes.c_void_p(264), 1 << 20, None) == B.EMD_ERR_WORKSPACE
+    assert L.emd_adjoint(fake, 8, 4, 1e-3, 10.0, 3, None, fake, None, fake, 1 << 20, None) == B.EMD_ERR_ARG
+    assert L.emd_decompose(fake, None, 8, 4, 1e-3, 10.0, None, None, None, fake, 1 << 20, None) == B.EMD_ERR_ARG
+    assert B.emd_status_string(B.EMD_ERR_LINESEARCH) == "linesearch did not terminate"
+
+
+def test_product_path_has_no_oracle_or_fallback():
+    """The package and the CUDA sources never reach into the oracle or the input generators."""
+    pkg = os.path.join(ROOT, "paper_1808_07284_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+(oracle|synth)\b", text, flags=re.M), f

@@ -1,0 +1,283 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (needs a GPU).
+
+Tolerances: dist within 1e-4 relative and phi within 1e-3 relative L2 after the same
+number of accepted iterations; u within 1e-3 relative L2; trial counts equal.  The GPU
+iterates are FP32 (rounding 6e-8 per step) and its inner products FP32 within a warp,
+FP64 above; the oracle is FP64 throughout.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import emd_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+DIST_RTOL = 1e-4
+PHI_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_07284_gb300 import build
+    build.build()
+    import paper_1808_07284_gb300 as P
+    return P
+
+
+def gpu_solve(P, obs, pred, dt, dx, **kw):
+    dev = torch.device("cuda:0")
+    o = torch.from_numpy(np.ascontiguousarray(obs, np.float32)).to(dev)
+    p = torch.from_numpy(np.ascontiguousarray(pred, np.float32)).to(dev)
+    check = kw.pop("check", True)
+    dist, phi, m, info = P.emd(o, p, dt, dx, check=check, **kw)
+    torch.cuda.synchronize()
+    m = m.double().cpu().numpy()
+    return dict(dist=dist, phi=phi.double().cpu().numpy(), ux=m[0], ut=m[1], info=info)
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def assert_parity(g, r, trials=True):
+    """Same accepted iterations; the same linesearch trials up to a rare near-tie decision
+    (the GPU tests the ratio of two FP64 sums of FP32 products, the oracle of FP64 norms);
+    then dist, phi and u within the stated tolerances."""
+    assert g["info"]["status"] == 0
+    assert g["info"]["iters"] == r["iters"]
+    if trials:
+        assert abs(g["info"]["ls_trials"] - r["trials"]) <= max(2, r["trials"] // 1000)
+    assert g["dist"] == pytest.approx(r["dist"], rel=DIST_RTOL)
+    assert g["info"]["dist_l1"] == pytest.approx(r["dist_l1"], rel=DIST_RTOL)
+    assert rel_l2(g["phi"], r["phi"]) <= PHI_RTOL
+    u_g = np.concatenate([g["ux"].ravel(), g["ut"].ravel()])
+    u_r = np.concatenate([r["ux"].ravel(), r["ut"].ravel()])
+    assert rel_l2(u_g, u_r) <= PHI_RTOL
+
+
+def test_small_gather_2000_iterations(pkg):
+    """Hyperbolic 256 x 64 gather, dt = 2 ms, dx = 10 m, mean balance, Algorithm 1, 2000 iterations."""
+    obs, pred = synth.gather_pair_hyperbolic()
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=2000)
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=2000)
+    assert_parity(g, r)
+    assert g["info"]["mass_mu"] == pytest.approx(2e-3 * 10.0 * O.mainini(obs, pred)[0].sum(), rel=1e-12)
+    assert g["info"]["imbalance"] == pytest.approx(r["imbalance"], rel=1e-9, abs=1e-12)
+    # the residual is a small difference (about 1% of f here): u's 1e-4 parity moves it by ~1%
+    assert g["info"]["r_feas"] == pytest.approx(r["r_feas"], rel=5e-2)
+    assert g["info"]["residual"] == pytest.approx(r["residual"], rel=5e-2)
+    assert g["info"]["duality_gap"] == pytest.approx(r["gap"], rel=1e-2, abs=1e-3 * r["dist"])
+
+
+def test_small_gather_normalised_domain(pkg):
+    """Same gather on Omega = [0,1]^2 (dt = 1/(nt-1), dx = 1/(nr-1)) as in the paper's runs."""
+    obs, pred = synth.gather_pair_hyperbolic()
+    dt, dx = 1 / 255, 1 / 63
+    r = O.pdhg(obs, pred, dt, dx, max_iter=500)
+    g = gpu_solve(pkg, obs, pred, dt, dx, max_iter=500)
+    assert_parity(g, r)
+
+
+SHAPES = [(1, 2), (1, 37), (2, 2), (3, 5), (17, 130), (33, 251), (9, 1000), (40, 121)]
+
+
+@pytest.mark.parametrize("nr,nt", SHAPES)
+def test_ragged_shapes(pkg, nr, nt):
+    rng = np.random.default_rng(nr * 1000 + nt)
+    obs, pred = synth.gather_pair_hyperbolic(nt=max(nt, 8), nr=nr, dt=2e-3, seed=nr + nt)
+    obs, pred = obs[:, :nt].copy(), pred[:, :nt].copy()
+    pred += 0.05 * rng.standard_normal(pred.shape).astype(np.float32)
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150)
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=150)
+    assert_parity(g, r)
+
+
+@pytest.mark.parametrize("tile", range(1, 7))
+def test_every_tile_shape(pkg, tile):
+    """Each compiled tile shape gives the oracle's iterates on a gather spanning several tiles."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=300, nr=37, seed=5)
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=120)
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=120, tile=tile)
+    assert_parity(g, r)
+
+
+def test_fixed_step_mode(pkg):
+    obs, pred = synth.gather_pair_hyperbolic(nt=128, nr=24, seed=3)
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=400, linesearch=0)
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=400, linesearch=0)
+    assert_parity(g, r)
+
+
+def test_no_balancing(pkg):
+    obs, pred = synth.gather_pair_hyperbolic(nt=128, nr=16, seed=4)
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=300, balance=O.BAL_NONE)
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=300, balance=0)
+    assert_parity(g, r)
+
+
+def test_plain_launches_equal_graph_replays(pkg):
+    obs, pred = synth.gather_pair_hyperbolic(nt=200, nr=20, seed=6)
+    a = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=130, launch_mode=0)
+    b = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=130, launch_mode=1)
+    assert a["info"]["iters"] == b["info"]["iters"] == 130
+    assert a["dist"] == pytest.approx(b["dist"], rel=1e-9)
+    assert rel_l2(a["phi"], b["phi"]) <= 1e-6
+
+
+def test_tolerance_stopping(pkg):
+    """tol > 0 stops at the first multiple of check_every whose residual is <= tol
+    (normalised domain, where FP32 iterates resolve the steps; see the precision notes)."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=96, nr=12, seed=3)
+    dt, dx = 1 / 95, 1 / 11
+    r = O.pdhg(obs, pred, dt, dx, max_iter=8000, tol=1e-2, check_every=10)
+    g = gpu_solve(pkg, obs, pred, dt, dx, max_iter=8000, tol=1e-2, check_every=10)
+    assert r["iters"] < 8000
+    assert g["info"]["iters"] % 10 == 0 and g["info"]["iters"] < 8000
+    assert g["info"]["residual"] <= 1e-2
+    # the residual is not monotone near the tolerance: the crossing may shift a little
+    assert abs(g["info"]["iters"] - r["iters"]) <= 0.2 * r["iters"]
+    assert g["dist"] == pytest.approx(r["dist"], rel=1e-3)
+
+
+def test_warm_start(pkg):
+    obs, pred = synth.gather_pair_hyperbolic(nt=96, nr=10, seed=8)
+    rng = np.random.default_rng(1)
+    phi0 = (0.01 * rng.standard_normal(obs.shape)).astype(np.float32)
+    m0 = (0.001 * rng.standard_normal((2,) + obs.shape)).astype(np.float32)
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=100, phi_init=phi0.astype(float),
+               m_init=np.stack([np.where(np.arange(10)[:, None] > 0, m0[0], 0),
+                                np.where(np.arange(96)[None, :] > 0, m0[1], 0)]))
+    dev = torch.device("cuda:0")
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=100,
+                  phi_init=torch.from_numpy(phi0).to(dev), m_init=torch.from_numpy(m0).to(dev))
+    assert_parity(g, r)
+
+
+def test_1d_shift_sweep_matches_closed_form(pkg):
+    """nt = 1024 on [0, 1] (dt = 1/(nt-1)), 8 Hz Ricker shifted: the same iterates as the
+    oracle after 800 iterations, and, run on, the distance of the closed-form W1."""
+    dt, obs, preds = synth.shift_sweep_1d(nt=1024, shifts=[-0.06, 0.03, 0.2])
+    for s, pred in preds:
+        r = O.pdhg(obs, pred, dt, 1.0, max_iter=800)
+        g = gpu_solve(pkg, obs, pred, dt, 1.0, max_iter=800)
+        assert_parity(g, r)
+        f = O.source_term(obs, pred)[0]
+        w = O.w1_1d(np.maximum(f, 0), np.maximum(-f, 0), dt)
+        c = gpu_solve(pkg, obs, pred, dt, 1.0, max_iter=200000, tol=1e-7)
+        assert c["info"]["dist_l1"] == pytest.approx(w, rel=1e-3), (s, c["info"])
+
+
+def test_decompose(pkg):
+    obs, pred = synth.gather_pair_transmissive(nt=500, nr=40, seed=9)
+    dev = torch.device("cuda:0")
+    o = torch.from_numpy(obs).to(dev)
+    p = torch.from_numpy(pred).to(dev)
+    mu = torch.empty_like(o)
+    nu = torch.empty_like(o)
+    mm, mn = pkg.emd_decompose(o, p, 1e-3, 12.5, mu, nu)
+    # elementwise in FP32: max and one add, the same operations the oracle does in FP64
+    mu_ref = np.maximum(pred, 0) + np.maximum(-obs, 0)
+    nu_ref = np.maximum(obs, 0) + np.maximum(-pred, 0)
+    np.testing.assert_array_equal(mu.cpu().numpy(), mu_ref.astype(np.float32))
+    np.testing.assert_array_equal(nu.cpu().numpy(), nu_ref.astype(np.float32))
+    m64, n64 = O.mainini(obs, pred)
+    assert mm == pytest.approx(1e-3 * 12.5 * m64.sum(), rel=1e-12)
+    assert mn == pytest.approx(1e-3 * 12.5 * n64.sum(), rel=1e-12)
+
+
+def test_adjoint_and_autograd(pkg):
+    obs, pred = synth.gather_pair_hyperbolic(nt=128, nr=16, seed=10)
+    dt, dx = 2e-3, 10.0
+    dev = torch.device("cuda:0")
+    o = torch.from_numpy(obs).to(dev).requires_grad_(True)
+    p = torch.from_numpy(pred).to(dev).requires_grad_(True)
+    loss = pkg.emd_loss(p, o, dt, dx, max_iter=300)
+    (3.0 * loss).backward()
+    r = O.pdhg(obs, pred, dt, dx, max_iter=300)
+    g_ref, go_ref = O.adjoint_source(r["phi"], dt, dx, grad_out=3.0)
+    assert loss.item() == pytest.approx(r["dist"], rel=DIST_RTOL)
+    assert rel_l2(p.grad.double().cpu().numpy(), g_ref) <= PHI_RTOL
+    assert rel_l2(o.grad.double().cpu().numpy(), go_ref) <= PHI_RTOL
+    gp = p.grad.double().cpu().numpy()
+    assert abs(gp.mean()) <= 1e-6 * np.abs(gp).max()
+
+
+def test_batched_equals_single(pkg):
+    """Uneven gathers solved together give each gather's own single-solve result."""
+    pairs = [synth.gather_pair_hyperbolic(nt=nt, nr=nr, seed=s)
+             for s, (nt, nr) in enumerate([(200, 17), (96, 40), (333, 9), (64, 1)])]
+    dev = torch.device("cuda:0")
+    O_ = [torch.from_numpy(o).to(dev) for o, _ in pairs]
+    P_ = [torch.from_numpy(p).to(dev) for _, p in pairs]
+    d, phis, ms, infos = pkg.emd_batched(O_, P_, 2e-3, 10.0, max_iter=200)
+    for b, (o, p) in enumerate(pairs):
+        r = O.pdhg(o, p, 2e-3, 10.0, max_iter=200)
+        g = dict(dist=d[b], phi=phis[b].double().cpu().numpy(), ux=ms[b][0].double().cpu().numpy(),
+                 ut=ms[b][1].double().cpu().numpy(), info=infos[b])
+        assert_parity(g, r)
+
+
+def test_batched_with_tolerance_stops_each_gather(pkg):
+    shapes = [(96, 12, 3), (72, 12, 6), (100, 10, 8)]
+    pairs = [synth.gather_pair_hyperbolic(nt=nt, nr=nr, seed=s) for nt, nr, s in shapes]
+    dts = [1 / (nt - 1) for nt, _, _ in shapes]
+    dxs = [1 / (nr - 1) for _, nr, _ in shapes]
+    dev = torch.device("cuda:0")
+    O_ = [torch.from_numpy(o).to(dev) for o, _ in pairs]
+    P_ = [torch.from_numpy(p).to(dev) for _, p in pairs]
+    d, phis, ms, infos = pkg.emd_batched(O_, P_, dts, dxs, max_iter=8000, tol=1e-2)
+    its = [i["iters"] for i in infos]
+    assert len(set(its)) > 1  # the gathers stop at different iterations
+    for b, (o, p) in enumerate(pairs):
+        assert infos[b]["residual"] <= 1e-2 and its[b] < 8000
+        r = O.pdhg(o, p, dts[b], dxs[b], max_iter=8000, tol=1e-2)
+        assert abs(its[b] - r["iters"]) <= 0.2 * r["iters"]
+        assert d[b] == pytest.approx(r["dist"], rel=1e-3)
+
+
+def test_nan_input_reports_nonfinite(pkg):
+    obs, pred = synth.gather_pair_hyperbolic(nt=64, nr=8)
+    pred[3, 10] = np.nan
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=50, check=False)
+    assert g["info"]["status"] == pkg.EMD_ERR_NONFINITE
+
+
+def test_linesearch_failure_is_reported(pkg):
+    obs, pred = synth.gather_pair_hyperbolic(nt=64, nr=8)
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=50, debug_fault=1, check=False)
+    assert g["info"]["status"] == pkg.EMD_ERR_LINESEARCH
+    assert g["info"]["iters"] == 0 and g["info"]["ls_trials"] == 40
+
+
+def test_transmissive_full_size_sampled(pkg):
+    """The 3000 x 400 gather at full size: same iterates as the oracle after 25 iterations."""
+    obs, pred = synth.gather_pair_transmissive()
+    r = O.pdhg(obs, pred, 1e-3, 12.5, max_iter=25)
+    g = gpu_solve(pkg, obs, pred, 1e-3, 12.5, max_iter=25)
+    assert_parity(g, r)
+
+
+def test_transmissive_converged_properties(pkg):
+    """The 3000 x 400 gather on Omega = [0,1]^2 run to residual 1e-3; then feasibility, the
+    distance and the duality gap recomputed on the host in FP64 from the returned u, phi."""
+    obs, pred = synth.gather_pair_transmissive()
+    dt, dx = 1 / 2999, 1 / 399
+    g = gpu_solve(pkg, obs, pred, dt, dx, max_iter=100000, tol=1e-3)
+    info = g["info"]
+    assert info["status"] == 0 and info["residual"] <= 1e-3 and info["iters"] < 100000
+    f = O.source_term(obs, pred)
+    res = O.divergence(g["ux"], g["ut"], dt, dx) + f
+    assert np.linalg.norm(res) / np.linalg.norm(f) == pytest.approx(info["r_feas"], rel=0.05, abs=2e-6)
+    val, l1 = O.objective(g["ux"], g["ut"], 1e-4)
+    assert info["dist"] == pytest.approx(dx * dt * val, rel=1e-5)
+    assert info["dist_l1"] == pytest.approx(dx * dt * l1, rel=1e-5)
+    gap = O.duality_gap(g["ux"], g["ut"], g["phi"], f, 1e-4, dt, dx)
+    assert info["duality_gap"] == pytest.approx(gap, rel=2e-2, abs=1e-3 * info["dist"])
