@@ -59,7 +59,7 @@ typedef enum {
  * Solver parameters (Sec. 2.2 and Algorithm 1).  emd_default_params() fills the paper's
  * constants: eps = 1e-4, xi = 0.5, zeta = 0.99, delta = 1e5, plus max_iter = 2000,
  * tol = 0, check_every = 10, ls_max_trials = 40, linesearch = 1, ls_norm = 2,
- * balance = EMD_BAL_MEAN, no warm start, tile = 0, launch_mode = 0.
+ * balance = EMD_BAL_MEAN, no warm start, tile = 0, launch_mode = 0, no trace.
  */
 typedef struct {
   double eps;        /* regularisation epsilon of Phi = ||u||_{1,1} + eps/2 ||u||^2      */
@@ -83,6 +83,11 @@ typedef struct {
   int launch_mode;   /* 0: passes replayed from a captured CUDA graph; 1: plain launches */
   int debug_fault;   /* fault injection for tests: 0 = off, 1 = every linesearch trial
                         fails (exercises EMD_ERR_LINESEARCH); never set in production   */
+  double *trace;     /* optional per-iteration history, device, B x max_iter x 4 doubles
+                        (gather-major): for iteration k, alpha_{k+1}, theta_{k+1}, the
+                        linesearch trials it took, and ||div u^{k+1} + f|| / ||f||.
+                        Entries past a gather's last iteration are left untouched.
+                        NULL = no history.                                                */
 } emd_params;
 
 /* Host-side result of one solve.  Distances are in the units of dx*dt*|u|. */

@@ -219,7 +219,10 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
 
     Returns a dict with dist, dist_l1, phi, ux, ut, iters, trials, status, residual,
     r_feas, r_step, alpha, theta, imbalance, gap (and a per-iteration ``trace`` when
-    ``record`` is set: alpha, theta, trials, r_feas, r_step).
+    ``record`` is set: alpha, theta, trials, r_feas, r_step, and the smallest relative gap
+    |lhs - rhs| / rhs between the two sides of the linesearch test over the iteration's
+    trials -- a near tie there is where a computation in other precision may decide
+    differently).
     """
     p = params if params is not None else Params()
     if kw:
@@ -259,6 +262,7 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
         if p.linesearch:
             a = alpha * math.sqrt(1.0 + theta)
             accepted = False
+            margin = math.inf  # closest any trial of this iteration came to the test's threshold
             for trial in range(1, p.ls_max_trials + 1):
                 th = a / alpha
                 beta = p.delta * a
@@ -270,6 +274,8 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
                 trials_total += 1
                 lhs = math.sqrt(p.delta) * a * _norm_vec(gdx, gdt, p.ls_norm)
                 rhs = p.zeta * _norm_scalar(dphi, p.ls_norm)
+                if rhs > 0:
+                    margin = min(margin, abs(lhs - rhs) / rhs)
                 if lhs <= rhs:
                     accepted = True
                     break
@@ -280,6 +286,7 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
             alpha, theta = a, th
         else:
             trial = 1
+            margin = math.inf
             nphi = dual_step(phi, 2.0 * nux - ux, 2.0 * nut - ut, f, beta, dt, dx)
             trials_total += 1
         res = divergence(nux, nut, dt, dx) + f
@@ -291,7 +298,7 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
         ux, ut, phi = nux, nut, nphi
         iters = k + 1
         if record:
-            trace.append((alpha, theta, trial, r_feas, r_step))
+            trace.append((alpha, theta, trial, r_feas, r_step, margin))
         if not (np.isfinite(phi).all() and np.isfinite(ux).all() and np.isfinite(ut).all()):
             status = STATUS_NONFINITE
             break

@@ -34,6 +34,7 @@ class EmdParams(ctypes.Structure):
         ("linesearch", c_int), ("ls_norm", c_int), ("balance", c_int),
         ("phi_init", c_void_p), ("m_init", c_void_p),
         ("tile", c_int), ("launch_mode", c_int), ("debug_fault", c_int),
+        ("trace", c_void_p),
     ]
 
 
@@ -125,7 +126,7 @@ def emd_default_params(**overrides) -> EmdParams:
     for k, v in overrides.items():
         if not hasattr(p, k):
             raise TypeError(f"unknown parameter {k}")
-        if k in ("phi_init", "m_init"):
+        if k in ("phi_init", "m_init", "trace"):
             v = _ptr(v)
         setattr(p, k, v)
     return p

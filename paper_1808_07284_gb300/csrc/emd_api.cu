@@ -260,6 +260,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   ctl.acc = acc;
   ctl.tile_shot = dtiles;
   ctl.n_done = n_done;
+  ctl.trace = p.trace;
 
   const size_t smem = smem_bytes(sh);
   EMD_CK(cudaFuncSetAttribute(sh.iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -348,6 +349,7 @@ void emd_default_params(emd_params *p) {
   p->tile = 0;
   p->launch_mode = 0;
   p->debug_fault = 0;
+  p->trace = nullptr;
 }
 
 int emd_tile_count(void) { return kNumShapes; }

@@ -75,6 +75,7 @@ struct Ctl {
   double *acc;                      // [gather][kSpread][kAcc] FP64 accumulators (zeroed)
   const int *tile_shot;             // global tile -> gather
   int *n_done;                      // gathers finished
+  double *trace;                    // optional [gather][max_iter][4] history (or null)
 };
 
 enum { ST_OK = 0, ST_NONFINITE = 3, ST_LINESEARCH = 4 };
@@ -176,7 +177,7 @@ __device__ __forceinline__ void publish(State *st, double eps) {
 // Linesearch decision of Algorithm 1 from the sums of pass k (one thread).
 // a: 0 P_pp, 1 P_pq, 2 P_qq, 3 G_pp, 4 G_pq, 5 G_qq, 6 sum|u|, 7 sum u^2, 8 sum du^2.
 // Trial t uses a = alpha_k s, s = sqrt(1 + theta_k) xi^(t-1), so no division is needed.
-__device__ void decide(const Ctl &c, State *st, const double (&a_)[9]) {
+__device__ void decide(const Ctl &c, State *st, const double (&a_)[9], int gather) {
   const double Ppp = a_[0], Ppq = a_[1], Pqq = a_[2], Gpp = a_[3], Gpq = a_[4], Gqq = a_[5];
   double fin = 0.0;
 #pragma unroll
@@ -186,6 +187,8 @@ __device__ void decide(const Ctl &c, State *st, const double (&a_)[9]) {
   st->s_u2 = a_[7];
   st->s_du2 = a_[8];
   bool done = false;
+  const int k0 = st->k;
+  int trials_now = 1;
   if (!isfinite(fin)) {
     st->status = ST_NONFINITE;
     done = true;
@@ -204,6 +207,7 @@ __device__ void decide(const Ctl &c, State *st, const double (&a_)[9]) {
       }
       s *= c.xi;
     }
+    trials_now = ok ? t : c.ls_max_trials;
     if (ok) {
       st->theta = s;
       st->alpha = ak * s;
@@ -222,6 +226,13 @@ __device__ void decide(const Ctl &c, State *st, const double (&a_)[9]) {
     st->trials += 1;
     st->k += 1;
     publish(st, c.eps);
+  }
+  if (c.trace && k0 < c.max_iter) {
+    double *e = c.trace + (static_cast<size_t>(gather) * c.max_iter + k0) * 4;
+    e[0] = st->alpha;
+    e[1] = st->theta;
+    e[2] = static_cast<double>(trials_now);
+    e[3] = st->fnorm > 0.0 ? sqrt(Ppp) / st->fnorm : sqrt(Ppp);
   }
   const int k = st->k;
   if (!done && k >= c.max_iter) done = true;
@@ -537,7 +548,7 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
   double a_[9];
   gather_totals<9>(acc, a_);
   if (threadIdx.x == 0) {
-    decide(c, st, a_);
+    decide(c, st, a_, s);
     st->ticket = 0u;
   }
 }
