@@ -174,6 +174,28 @@ emd_status emd_adjoint(const float *phi, int nt, int nr, double dt, double dx, i
                        const float *grad_out, float *grad_pred, float *grad_obs,
                        void *workspace, size_t ws_bytes, emd_stream_t stream);
 
+/*
+ * emd_dyn_solve without a workspace argument, for callers that cannot allocate device
+ * memory: code running during stream capture into a CUDA graph, code whose framework
+ * allocator owns all device memory, or loops that must never block on an allocation.
+ * The paper has no counterpart; this is a deployment convenience.
+ *
+ * Scratch space is a 16 MiB array compiled into the library (every GPU that loads the
+ * library holds it until the process exits), so the gather must satisfy
+ * emd_workspace_size(nt, nr) <= 16 MiB (about 450k cells, e.g. 1024 x 400); larger
+ * gathers return EMD_ERR_WORKSPACE without launching anything.  Arguments, outputs and
+ * results are those of emd_dyn_solve; the passes run as plain kernel launches (no CUDA
+ * graph is instantiated) and nothing calls cudaMalloc or cudaFree.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress with that device
+ * current); make that first call before any stream capture.  Every call on a device
+ * shares the one array, which keeps the last call's contents (each call re-initialises
+ * what it needs): calls that overlap on the GPU (different streams, or different host
+ * threads without ordering) race and give wrong results.
+ */
+emd_status emd_dyn_solve_noalloc(const float *f_obs, const float *f_pred, int nt, int nr,
+                                 double dt, double dx, const emd_params *params, float *phi,
+                                 float *m, emd_result *result, emd_stream_t stream);
+
 /* Static, human-readable name of a status code. */
 const char *emd_status_string(emd_status s);
 

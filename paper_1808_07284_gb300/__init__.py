@@ -17,13 +17,13 @@ from ._binding import (  # noqa: F401
     EMD_BAL_MEAN, EMD_BAL_NONE, EMD_ERR_ARG, EMD_ERR_CUDA, EMD_ERR_LINESEARCH,
     EMD_ERR_NONFINITE, EMD_ERR_TIMEOUT, EMD_ERR_WORKSPACE, EMD_OK, EXPORTS,
     EmdError, EmdParams, EmdResult, emd_adjoint, emd_batched_workspace_size, emd_decompose,
-    emd_default_params, emd_dyn_solve, emd_dyn_solve_batched, emd_status_string,
+    emd_default_params, emd_dyn_solve, emd_dyn_solve_batched, emd_dyn_solve_noalloc, emd_status_string,
     emd_tile_count, emd_workspace_size, lib, new_workspace,
 )
 
 __all__ = [
     "emd", "emd_batched", "emd_loss", "EMDFunction", "emd_decompose", "emd_dyn_solve",
-    "emd_dyn_solve_batched", "emd_adjoint", "emd_default_params", "emd_workspace_size",
+    "emd_dyn_solve_batched", "emd_dyn_solve_noalloc", "emd_adjoint", "emd_default_params", "emd_workspace_size",
     "emd_batched_workspace_size", "emd_status_string", "emd_tile_count", "EmdError",
 ]
 

@@ -20,7 +20,7 @@ EMD_BAL_NONE, EMD_BAL_MEAN = 0, 1
 EXPORTS = (
     "emd_default_params", "emd_tile_count", "emd_workspace_size", "emd_decompose",
     "emd_dyn_solve", "emd_batched_workspace_size", "emd_dyn_solve_batched", "emd_adjoint",
-    "emd_status_string",
+    "emd_status_string", "emd_dyn_solve_noalloc",
 )
 
 
@@ -93,6 +93,9 @@ def lib() -> ctypes.CDLL:
         L.emd_adjoint.argtypes = [c_void_p, c_int, c_int, c_double, c_double, c_int, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
         L.emd_adjoint.restype = c_int
+        L.emd_dyn_solve_noalloc.argtypes = [c_void_p, c_void_p, c_int, c_int, c_double, c_double,
+                                            P(EmdParams), c_void_p, c_void_p, P(EmdResult), c_void_p]
+        L.emd_dyn_solve_noalloc.restype = c_int
         L.emd_status_string.argtypes = [c_int]
         L.emd_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -223,3 +226,19 @@ def emd_adjoint(phi, dt, dx, balance, grad_out, grad_pred, grad_obs, workspace, 
                            _ptr(grad_obs), _ptr(workspace), workspace.numel(), _stream(stream))
     if st != EMD_OK:
         raise EmdError(st, "emd_adjoint")
+
+
+def emd_dyn_solve_noalloc(f_obs, f_pred, dt, dx, params: EmdParams, phi, m, stream=None,
+                          check: bool = True) -> EmdResult:
+    """emd_dyn_solve on the library's built-in scratch array (no workspace, no allocation)."""
+    nr, nt = f_obs.shape
+    _check_grid(f_obs, nr, nt, "f_obs")
+    _check_grid(f_pred, nr, nt, "f_pred")
+    _check_grid(phi, nr, nt, "phi")
+    _check_grid(m, nr, nt, "m", planes=2)
+    res = EmdResult()
+    st = lib().emd_dyn_solve_noalloc(_ptr(f_obs), _ptr(f_pred), nt, nr, dt, dx, ctypes.byref(params),
+                                     _ptr(phi), _ptr(m), ctypes.byref(res), _stream(stream))
+    if check and st != EMD_OK:
+        raise EmdError(st, "emd_dyn_solve_noalloc")
+    return res

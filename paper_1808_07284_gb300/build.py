@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libemd_gb300.so")
-SOURCES = [os.path.join(HERE, "csrc", "emd_api.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "emd_api.cu"), os.path.join(HERE, "csrc", "emd_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "emd_kernels.cuh"),
                   os.path.join(ROOT, "include", "emd_gb300.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
