@@ -67,7 +67,8 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1808_07284_gb300/csrc/emd_kernels.cuh", "paper_1808_07284_gb300/csrc/emd_api.cu"):
+    for rel in ("paper_1808_07284_gb300/csrc/emd_kernels.cuh", "paper_1808_07284_gb300/csrc/emd_pass_tma.cuh",
+                "paper_1808_07284_gb300/csrc/emd_api.cu"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -11,6 +11,7 @@
 
 #include "emd_gb300.h"
 #include "emd_kernels.cuh"
+#include "emd_pass_tma.cuh"
 
 namespace {
 
@@ -28,21 +29,64 @@ using emd::State;
     }                                              \
   } while (0)
 
-// Stencil tile shapes (TI rows x (W - 8) time samples per CTA); id = index + 1.
+// Stencil tile shapes (TI rows x (W - 8) time samples per tile); id = index + 1.
+// `iter_tma` marks the persistent TMA-staged pass (its finalize pass is the plain one
+// with the same tiling).
 struct Shape {
   int ti, w;
   void (*iter)(Ctl);
   void (*fin)(Ctl);
+  void (*iter_tma)(Ctl, int);
 };
 
 #define EMD_SHAPE(TI, W) \
-  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true> }
+  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr }
+constexpr int kTmaTI = 13;
 const Shape kShapes[] = {EMD_SHAPE(16, 128), EMD_SHAPE(8, 128), EMD_SHAPE(32, 128),
-                         EMD_SHAPE(8, 256),  EMD_SHAPE(16, 256), EMD_SHAPE(1, 256)};
+                         EMD_SHAPE(8, 256),  EMD_SHAPE(16, 256), EMD_SHAPE(1, 256),
+                         Shape{kTmaTI, 128, nullptr, emd::k_pass<kTmaTI, 128, true>,
+                               emd::k_pass_tma<kTmaTI>}};
 #undef EMD_SHAPE
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+constexpr int kTmaShape = kNumShapes - 1;
 
+// Dynamic shared memory of the plain pass / finalize pass of a shape, and of its
+// iteration pass.
 size_t smem_bytes(const Shape &s) { return sizeof(float) * 6u * (s.ti + 4) * s.w; }
+size_t iter_smem_bytes(const Shape &s) {
+  return s.iter_tma ? emd::TmaTile<kTmaTI>::SMEM : smem_bytes(s);
+}
+
+// cuTensorMapEncodeTiled, reached through the runtime (no link against libcuda).
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();
+      return static_cast<EncodeTiled>(nullptr);
+    }
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// Multiprocessors of the current device (the persistent pass runs two CTAs on each).
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    (void)cudaGetLastError();
+    return 148;
+  }
+  return n;
+}
 
 size_t align256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
 int ntp_of(int nt) { return (nt + 31) / 32 * 32; }
@@ -109,9 +153,10 @@ int pick_shape(const emd_params &p, int B, const int *nt, const int *nr) {
   int nr_max = 0;
   for (int b = 0; b < B; ++b) nr_max = std::max(nr_max, nr[b]);
   (void)nt;
-  if (nr_max == 1) return 5;  // 1 x 248: one receiver
-  if (nr_max <= 8) return 1;  // 8 x 120
-  return 0;                   // 16 x 120
+  if (nr_max == 1) return 5;          // 1 x 248: one receiver
+  if (nr_max <= 8) return 1;          // 8 x 120
+  if (encode_fn()) return kTmaShape;  // 13 x 120, persistent, TMA-staged
+  return 0;                           // 16 x 120
 }
 
 bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
@@ -125,8 +170,11 @@ constexpr int kPoll = 64;
 class PassLauncher {
  public:
   static constexpr int kChunk = 32;
-  PassLauncher(const Shape &sh, const Ctl &ctl, int grid, size_t smem, int mode)
-      : sh_(sh), ctl_(ctl), grid_(grid), smem_(smem), mode_(mode) {}
+  PassLauncher(const Shape &sh, const Ctl &ctl, int tiles, int mode)
+      : sh_(sh), ctl_(ctl), tiles_(tiles), mode_(mode) {
+    smem_ = iter_smem_bytes(sh);
+    grid_ = sh.iter_tma ? std::min(tiles, 2 * sm_count()) : tiles;
+  }
   ~PassLauncher() {
     if (exec_) cudaGraphExecDestroy(exec_);
     if (graph_) cudaGraphDestroy(graph_);
@@ -137,18 +185,24 @@ class PassLauncher {
       if (!exec_ && capture() != EMD_OK) return EMD_ERR_CUDA;
       for (; done + kChunk <= n; done += kChunk) EMD_CK(cudaGraphLaunch(exec_, stream));
     }
-    for (; done < n; ++done) sh_.iter<<<grid_, kThreads, smem_, stream>>>(ctl_);
+    for (; done < n; ++done) one(stream);
     EMD_CK(cudaGetLastError());
     return EMD_OK;
   }
 
  private:
+  void one(cudaStream_t s) {
+    if (sh_.iter_tma)
+      sh_.iter_tma<<<grid_, emd::kTmaThreads, smem_, s>>>(ctl_, tiles_);
+    else
+      sh_.iter<<<grid_, kThreads, smem_, s>>>(ctl_);
+  }
   emd_status capture() {
     cudaStream_t cs;
     EMD_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      for (int i = 0; i < kChunk; ++i) sh_.iter<<<grid_, kThreads, smem_, cs>>>(ctl_);
+      for (int i = 0; i < kChunk; ++i) one(cs);
       ok = cudaStreamEndCapture(cs, &graph_) == cudaSuccess;
     }
     if (ok) ok = cudaGraphInstantiate(&exec_, graph_, 0) == cudaSuccess;
@@ -161,12 +215,25 @@ class PassLauncher {
   }
   const Shape &sh_;
   Ctl ctl_;
-  int grid_;
-  size_t smem_;
-  int mode_;
+  int tiles_, grid_ = 0, mode_;
+  size_t smem_ = 0;
   cudaGraph_t graph_ = nullptr;
   cudaGraphExec_t exec_ = nullptr;
 };
+
+// Fills S.tmap: the gather's nine planes as one 3D float tensor {ntp, nr, 9} with
+// strides (ntp * 4, plane bytes) and a box of (TI + 4) rows x 128 samples.
+bool encode_tmap(Shot &S, void *base, size_t plane_bytes) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(S.ntp), static_cast<cuuint64_t>(S.nr), 9u};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(S.ntp) * 4u, plane_bytes};
+  const cuuint32_t box[3] = {128u, static_cast<cuuint32_t>(emd::TmaTile<kTmaTI>::R), 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return enc(&S.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
                       const int *nr, const double *dt, const double *dx, const emd_params *pp,
@@ -188,7 +255,8 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   const Layout L = layout(B, nt, nr);
   if (!ws || !aligned256(ws) || ws_bytes < L.total) return EMD_ERR_WORKSPACE;
 
-  const int si = pick_shape(p, B, nt, nr);
+  int si = pick_shape(p, B, nt, nr);
+  if (kShapes[si].iter_tma && !encode_fn()) si = 0;  // no TMA descriptors: plain staging
   const Shape &sh = kShapes[si];
   char *base = static_cast<char *>(ws);
 
@@ -207,15 +275,16 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     S.nt = nt[b];
     S.nr = nr[b];
     S.ntp = ntp_of(nt[b]);
-    S.plane = nr[b] * S.ntp;
     const size_t pl = L.plane[b];
     char *g = base + L.gather[b];
     S.f = reinterpret_cast<float *>(g);
-    // u[m] spans two plane slots; its t plane is addressed as x plane + `plane` floats,
-    // which stays inside the pair because plane * 4 <= pl (and is 128-byte aligned).
-    for (int u = 0; u < 3; ++u) S.u[u] = reinterpret_cast<float *>(g + (1 + 2 * u) * pl);
+    for (int u = 0; u < 3; ++u) {
+      S.ux[u] = reinterpret_cast<float *>(g + (1 + 2 * u) * pl);
+      S.ut[u] = reinterpret_cast<float *>(g + (2 + 2 * u) * pl);
+    }
     S.ph[0] = reinterpret_cast<float *>(g + 7 * pl);
     S.ph[1] = reinterpret_cast<float *>(g + 8 * pl);
+    if (sh.iter_tma && !encode_tmap(S, g, pl)) return EMD_ERR_CUDA;
     S.tiles_j = (nt[b] + (sh.w - 8) - 1) / (sh.w - 8);
     S.tile0 = static_cast<int>(tile_shot.size());
     S.ntiles = tiles_of(sh, nt[b], nr[b]);
@@ -233,13 +302,14 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   Shot *dshots = reinterpret_cast<Shot *>(base + L.shots);
   int *dtiles = reinterpret_cast<int *>(base + L.tiles);
   int *n_done = reinterpret_cast<int *>(base + L.misc);
+  int *err_flag = n_done + 1;
   double *acc = reinterpret_cast<double *>(base + L.acc);
 
   EMD_CK(cudaMemcpyAsync(dshots, shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
   EMD_CK(cudaMemcpyAsync(dtiles, tile_shot.data(), sizeof(int) * tile_shot.size(),
                          cudaMemcpyHostToDevice, stream));
   EMD_CK(cudaMemsetAsync(states, 0, sizeof(State) * B, stream));
-  EMD_CK(cudaMemsetAsync(n_done, 0, sizeof(int), stream));
+  EMD_CK(cudaMemsetAsync(n_done, 0, 2 * sizeof(int), stream));
   EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double) * emd::kSpread * emd::kAcc * B, stream));
 
   Ctl ctl{};
@@ -260,18 +330,23 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   ctl.acc = acc;
   ctl.tile_shot = dtiles;
   ctl.n_done = n_done;
+  ctl.error = err_flag;
   ctl.trace = p.trace;
 
   const size_t smem = smem_bytes(sh);
-  EMD_CK(cudaFuncSetAttribute(sh.iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(smem)));
+  if (sh.iter_tma)
+    EMD_CK(cudaFuncSetAttribute(sh.iter_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(iter_smem_bytes(sh))));
+  else
+    EMD_CK(cudaFuncSetAttribute(sh.iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem)));
   EMD_CK(cudaFuncSetAttribute(sh.fin, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(smem)));
 
   emd::k_prepare<<<dim3(std::min(nr_max, 128), B), kThreads, 0, stream>>>(ctl);
   EMD_CK(cudaGetLastError());
 
-  PassLauncher passes(sh, ctl, grid, smem, p.launch_mode);
+  PassLauncher passes(sh, ctl, grid, p.launch_mode);
   if (p.tol <= 0.0) {
     const emd_status s = passes.launch(p.max_iter, stream);
     if (s != EMD_OK) return s;
@@ -295,8 +370,14 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   EMD_CK(cudaGetLastError());
 
   std::vector<State> hs(B);
+  int h_flags[2] = {0, 0};
   EMD_CK(cudaMemcpyAsync(hs.data(), states, sizeof(State) * B, cudaMemcpyDeviceToHost, stream));
+  EMD_CK(cudaMemcpyAsync(h_flags, n_done, sizeof(h_flags), cudaMemcpyDeviceToHost, stream));
   EMD_CK(cudaStreamSynchronize(stream));
+  if (h_flags[1]) {  // a bounded device wait gave up
+    for (int b = 0; b < B; ++b) results[b].status = EMD_ERR_TIMEOUT;
+    return EMD_ERR_TIMEOUT;
+  }
 
   emd_status first = EMD_OK;
   for (int b = 0; b < B; ++b) {

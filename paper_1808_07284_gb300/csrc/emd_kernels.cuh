@@ -24,25 +24,29 @@
 // one warp, everything above a warp is FP64 (FP64 atomics into L2).
 #pragma once
 
-#include <cstdint>
+#include <cuda.h>  // CUtensorMap (the TMA descriptor type); no driver API call is made here
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 namespace emd {
 
 constexpr int kThreads = 256;
 constexpr int kAcc = 12;  // FP64 accumulators per gather
 
-// Per-gather constants of one solve (device copy in the workspace).
+// Per-gather constants of one solve (device copy in the workspace).  A gather's nine
+// pitched planes sit at a uniform stride: z = 0 f, 1 + 2m ux[m], 2 + 2m ut[m], 7 + m ph[m];
+// `tmap` describes them as one 3D tensor {ntp, nr, 9} for the TMA pass.
 struct Shot {
+  CUtensorMap tmap;                 // TMA descriptor of the nine planes (TMA pass only)
   const float *p_obs, *p_pred;      // caller inputs [nr][nt]
   float *phi_out, *m_out;           // caller outputs [nr][nt], [2][nr][nt]
   const float *phi_init, *m_init;   // optional warm start (caller, may be null)
   float *f;                         // Pcal - Pobs, pitched [nr][ntp]
-  float *u[3];                      // u^m lives in u[m % 3]: x plane then t plane, pitched
+  float *ux[3], *ut[3];             // u^m lives in ux/ut[m % 3], pitched
   float *ph[2];                     // phi^m lives in ph[m & 1], pitched
   int nt, nr, ntp, tiles_j;         // ntp: row pitch in floats (multiple of 32)
   int tile0, ntiles;                // first global tile index and tile count of this gather
-  int plane;                        // nr * ntp
   float rdx, rdt;                   // 1/dx (0 when nr == 1), 1/dt
   double area, lambda;              // dx*dt (dt when nr == 1); 4/dx^2 + 4/dt^2
 };
@@ -65,7 +69,7 @@ struct alignas(16) State {
   unsigned int ticket;
 };
 
-constexpr int kSpread = 32;         // copies of each accumulator (spreads the atomics)
+constexpr int kSpread = 16;         // copies of each accumulator (spreads the atomics)
 // Solve-wide parameters, passed by value to every kernel.
 struct Ctl {
   double eps, xi, zeta, delta, tol, alpha0;
@@ -75,6 +79,7 @@ struct Ctl {
   double *acc;                      // [gather][kSpread][kAcc] FP64 accumulators (zeroed)
   const int *tile_shot;             // global tile -> gather
   int *n_done;                      // gathers finished
+  int *error;                       // set to 1 when a bounded device wait gives up
   double *trace;                    // optional [gather][max_iter][4] history (or null)
 };
 
@@ -111,9 +116,19 @@ __device__ __forceinline__ float shrinkf(float v, float a) {
   return av >= a ? copysignf(av - a, v) : 0.0f;
 }
 
+// Barrier over the kThreads compute threads: the whole CTA, or (NAMED) the compute
+// warps only, when a CTA also holds a producer warp that does not take part.
+template <bool NAMED>
+__device__ __forceinline__ void compute_sync() {
+  if (NAMED)
+    asm volatile("bar.sync 1, %0;\n" ::"n"(kThreads) : "memory");
+  else
+    __syncthreads();
+}
+
 // Reduce N per-thread FP32 partials of a CTA: FP32 within the warp, FP64 across warps,
-// then one FP64 atomic add per value into acc[0..N).  Every thread must call it.
-template <int N>
+// then one FP64 atomic add per value into acc[0..N).  Every compute thread must call it.
+template <int N, bool NAMED = false>
 __device__ __forceinline__ void block_accumulate(float (&v)[N], double *acc) {
   // acc points at this CTA's copy: acc[0..N)
   __shared__ float part[kThreads / 32][N];
@@ -123,7 +138,7 @@ __device__ __forceinline__ void block_accumulate(float (&v)[N], double *acc) {
     const float w = warp_sum(v[n]);
     if (lane == 0) part[warp][n] = w;
   }
-  __syncthreads();
+  compute_sync<NAMED>();
   if (threadIdx.x < N) {
     double s = 0.0;
 #pragma unroll
@@ -144,24 +159,27 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket, int nblocks) {
   return last;
 }
 
-// In the deciding CTA: sums the kSpread copies of the first N accumulators of a gather
-// (warp w takes values w, w + 8, ...), zeroes them for the next pass, and leaves the
-// totals in out[0..N).  Every thread must call it.
-template <int N>
+// In the deciding CTA: sums the kSpread copies of the first N (<= 16) accumulators of a
+// gather in one round (half-warp h of warp w takes value w + 8 h, one lane per copy),
+// zeroes them for the next pass, and leaves the totals in out[0..N).  Every thread.
+template <int N, bool NAMED = false>
 __device__ __forceinline__ void gather_totals(double *acc, double (&out)[N]) {
+  static_assert(kSpread == 16 && N <= 16, "one lane of a half-warp per copy");
   __shared__ double tot[N];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  static_assert(kSpread == 32, "one lane per copy");
-  for (int n = warp; n < N; n += kThreads / 32) {
-    double *a = acc + lane * kAcc + n;
-    double v = __ldcg(a);
+  const int n = warp + (kThreads / 32) * (lane >> 4);
+  double v = 0.0;
+  if (n < N) {
+    double *a = acc + (lane & 15) * kAcc + n;
+    v = __ldcg(a);
     *a = 0.0;
-    v = warp_sum_d(v);
-    if (lane == 0) tot[n] = v;
   }
-  __syncthreads();
 #pragma unroll
-  for (int n = 0; n < N; ++n) out[n] = tot[n];
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((lane & 15) == 0 && n < N) tot[n] = v;
+  compute_sync<NAMED>();
+#pragma unroll
+  for (int q = 0; q < N; ++q) out[q] = tot[q];
 }
 
 // ------------------------------------------------------------------------------ decision
@@ -174,70 +192,117 @@ __device__ __forceinline__ void publish(State *st, double eps) {
   st->inv_f = 1.0f / (1.0f + static_cast<float>(eps * st->alpha));
 }
 
-// Linesearch decision of Algorithm 1 from the sums of pass k (one thread).
-// a: 0 P_pp, 1 P_pq, 2 P_qq, 3 G_pp, 4 G_pq, 5 G_qq, 6 sum|u|, 7 sum u^2, 8 sum du^2.
-// Trial t uses a = alpha_k s, s = sqrt(1 + theta_k) xi^(t-1), so no division is needed.
-__device__ void decide(const Ctl &c, State *st, const double (&a_)[9], int gather) {
-  const double Ppp = a_[0], Ppq = a_[1], Pqq = a_[2], Gpp = a_[3], Gpq = a_[4], Gqq = a_[5];
-  double fin = 0.0;
+// What the decision needs besides the pass's sums: loaded and precomputed by the
+// deciding warp while the sums are still being gathered.
+struct DecidePrep {
+  double alpha, theta, coef, beta_fixed, fnorm;
+  double s_lane, s_lane2, base32;  // sqrt(1 + theta_k) xi^lane, its square, xi^32
+  double dak2;                      // delta alpha_k^2
+  int k;
+};
+
+__device__ __forceinline__ DecidePrep decide_prep(const Ctl &c, const State *st) {
+  const int lane = threadIdx.x & 31;
+  DecidePrep d;
+  d.k = st->k;
+  d.alpha = st->alpha;
+  d.theta = st->theta;
+  d.coef = st->coef;
+  d.beta_fixed = st->beta_fixed;
+  d.fnorm = st->fnorm;
+  double xl = 1.0, base = c.xi;  // xl = xi^lane; base ends as xi^32
 #pragma unroll
-  for (int n = 0; n < 9; ++n) fin += a_[n];
+  for (int b = 0; b < 5; ++b) {
+    if ((lane >> b) & 1) xl *= base;
+    base *= base;
+  }
+  d.base32 = base;
+  d.s_lane = sqrt(1.0 + d.theta) * xl;  // upper end of [alpha_k, alpha_k sqrt(1+theta_k)]
+  d.s_lane2 = d.s_lane * d.s_lane;
+  d.dak2 = c.delta * d.alpha * d.alpha;
+  return d;
+}
+
+// Linesearch decision of Algorithm 1 from the sums of pass k, taken by one warp.
+// a: 0 P_pp, 1 P_pq, 2 P_qq, 3 G_pp, 4 G_pq, 5 G_qq, 6 sum|u|, 7 sum u^2, 8 sum du^2.
+// Trial t (0-based) uses a = alpha_k s_t with s_t = sqrt(1 + theta_k) xi^t, so the trials
+// do not depend on each other: lane t tests trial t (32 at a time) and a ballot picks the
+// first that passes -- the same choice as Algorithm 1's sequential backtracking.
+// Only lane 0 writes the state.
+__device__ void decide(const Ctl &c, State *st, const DecidePrep &d, const double (&a_)[9],
+                       int gather) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const double Ppp = a_[0], Ppq = a_[1], Pqq = a_[2], Gpp = a_[3], Gpq = a_[4], Gqq = a_[5];
+  const bool finite = __all_sync(FULL, lane >= 9 || isfinite(a_[lane < 9 ? lane : 0]));
+  const int k0 = d.k;
+  bool done = false;
+  int trials_now = 1;
+  int status = ST_OK;
+  double alpha = d.alpha, theta = d.theta, coef = d.coef;
+  if (!finite) {
+    status = ST_NONFINITE;
+    done = true;
+  } else if (c.linesearch) {
+    const double z2 = c.zeta * c.zeta;
+    double s = d.s_lane, s2 = d.s_lane2, chunk2 = 1.0;
+    int found = -1;
+    double s_found = 0.0;
+    for (int t0 = 0; t0 < c.ls_max_trials && found < 0; t0 += 32) {
+      // delta a^2 ||grad p + s grad q||^2 <= zeta^2 ||p + s q||^2, a = alpha_k s
+      const double lhs = d.dak2 * s2 * (Gpp + s * (2.0 * Gpq + s * Gqq));
+      const double rhs = z2 * (Ppp + s * (2.0 * Ppq + s * Pqq));
+      const bool pass = t0 + lane < c.ls_max_trials && lhs <= rhs && c.debug_fault != 1;
+      const unsigned m = __ballot_sync(FULL, pass);
+      if (m) {
+        const int w = __ffs(m) - 1;
+        found = t0 + w;
+        s_found = __shfl_sync(FULL, s, w);
+      }
+      s *= d.base32;
+      chunk2 = d.base32 * d.base32;
+      s2 *= chunk2;
+    }
+    if (found >= 0) {
+      trials_now = found + 1;
+      theta = s_found;
+      alpha = d.alpha * s_found;
+      coef = c.delta * alpha;
+    } else {
+      trials_now = c.ls_max_trials;
+      status = ST_LINESEARCH;
+      done = true;
+    }
+  } else {
+    coef = d.beta_fixed;
+    theta = 1.0;
+  }
+  if (lane != 0) return;
   st->s_p2 = Ppp;
   st->s_u1 = a_[6];
   st->s_u2 = a_[7];
   st->s_du2 = a_[8];
-  bool done = false;
-  const int k0 = st->k;
-  int trials_now = 1;
-  if (!isfinite(fin)) {
-    st->status = ST_NONFINITE;
-    done = true;
-  } else if (c.linesearch) {
-    const double ak = st->alpha;
-    double s = sqrt(1.0 + st->theta);  // upper end of [alpha_k, alpha_k sqrt(1+theta_k)]
-    int t = 1;
-    bool ok = false;
-    for (; t <= c.ls_max_trials; ++t) {
-      const double a = ak * s;
-      const double lhs = c.delta * a * a * (Gpp + s * (2.0 * Gpq + s * Gqq));
-      const double rhs = c.zeta * c.zeta * (Ppp + s * (2.0 * Ppq + s * Pqq));
-      if (lhs <= rhs && c.debug_fault != 1) {
-        ok = true;
-        break;
-      }
-      s *= c.xi;
-    }
-    trials_now = ok ? t : c.ls_max_trials;
-    if (ok) {
-      st->theta = s;
-      st->alpha = ak * s;
-      st->coef = c.delta * st->alpha;
-      st->trials += t;
-      st->k += 1;
-      publish(st, c.eps);
-    } else {
-      st->trials += c.ls_max_trials;
-      st->status = ST_LINESEARCH;
-      done = true;
-    }
-  } else {
-    st->coef = st->beta_fixed;
-    st->theta = 1.0;
-    st->trials += 1;
-    st->k += 1;
+  st->trials += trials_now;
+  if (status == ST_OK) {
+    st->alpha = alpha;
+    st->theta = theta;
+    st->coef = coef;
+    st->k = k0 + 1;
     publish(st, c.eps);
+  } else {
+    st->status = status;
   }
   if (c.trace && k0 < c.max_iter) {
     double *e = c.trace + (static_cast<size_t>(gather) * c.max_iter + k0) * 4;
-    e[0] = st->alpha;
-    e[1] = st->theta;
+    e[0] = alpha;
+    e[1] = theta;
     e[2] = static_cast<double>(trials_now);
-    e[3] = st->fnorm > 0.0 ? sqrt(Ppp) / st->fnorm : sqrt(Ppp);
+    e[3] = d.fnorm > 0.0 ? sqrt(Ppp) / d.fnorm : sqrt(Ppp);
   }
-  const int k = st->k;
+  const int k = status == ST_OK ? k0 + 1 : k0;
   if (!done && k >= c.max_iter) done = true;
   if (!done && c.tol > 0.0 && k % c.check_every == 0) {
-    const double fnorm = st->fnorm;
+    const double fnorm = d.fnorm;
     const double r_feas = fnorm > 0.0 ? sqrt(Ppp) / fnorm : sqrt(Ppp);
     const double r_step = sqrt(a_[8]) / fmax(sqrt(a_[7]), 1e-30);
     st->r_feas = r_feas;
@@ -285,8 +350,8 @@ __global__ void __launch_bounds__(kThreads) k_prepare(Ctl c) {
       if (in && S.phi_init) ph = S.phi_init[g];
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        S.u[m][o] = m == 0 ? ux : 0.0f;
-        S.u[m][S.plane + o] = m == 0 ? ut : 0.0f;
+        S.ux[m][o] = m == 0 ? ux : 0.0f;
+        S.ut[m][o] = m == 0 ? ut : 0.0f;
       }
       S.ph[0][o] = 0.0f;
       S.ph[1][o] = ph;  // pass 0 reads phi^{-1} := phi_init from ph[1]
@@ -374,21 +439,19 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
   const float theta = __int_as_float(h1.x), inv = __int_as_float(h1.y);
   const float fmean = __int_as_float(h1.z);
 
-  const int nr = S.nr, nt = S.nt, ntp = S.ntp, plane = S.plane;
+  const int nr = S.nr, nt = S.nt, ntp = S.ntp;
   const float rdx = S.rdx, rdt = S.rdt;
   const int lt = gtile - S.tile0;
   const int i0 = (lt / S.tiles_j) * TI;
   const int j0 = (lt % S.tiles_j) * TJ;
 
-  const float *u_prev = S.u[k == 0 ? 0 : (k - 1) % 3];
-  const float *u_cur = S.u[k % 3];
-  float *u_next = S.u[(k + 1) % 3];
+  const int kp = k == 0 ? 0 : (k - 1) % 3, kc = k % 3, kn = (k + 1) % 3;
   const float *ph_prev = S.ph[(k + 1) & 1];
   float *ph_cur = S.ph[k & 1];
 
   // ---- stage the six input planes (rows i0-2.., columns j0-4..) into shared memory
   {
-    const float *src[6] = {u_prev, u_prev + plane, u_cur, u_cur + plane, ph_prev, S.f};
+    const float *src[6] = {S.ux[kp], S.ut[kp], S.ux[kc], S.ut[kc], ph_prev, S.f};
     constexpr int Q = W / 4;
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
@@ -483,8 +546,8 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
         nx = shrinkf(UBx[o] + alpha * gx, alpha) * inv;
         nt_ = shrinkf(UBt[o] + alpha * gt, alpha) * inv;
         if (r >= 2 && r < TI + 2 && c_ >= 4 && c_ < TJ + 4) {
-          u_next[gi * ntp + gj] = nx;
-          u_next[plane + gi * ntp + gj] = nt_;
+          S.ux[kn][gi * ntp + gj] = nx;
+          S.ut[kn][gi * ntp + gj] = nt_;
         }
       }
       UAx[o] = nx;
@@ -545,12 +608,12 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
   double *acc = c.acc + static_cast<size_t>(s) * kSpread * kAcc;
   block_accumulate<9>(v, acc + (lt % kSpread) * kAcc);
   if (!last_block(&st->ticket, S.ntiles)) return;
+  DecidePrep pr;
+  if (threadIdx.x < 32) pr = decide_prep(c, st);
   double a_[9];
   gather_totals<9>(acc, a_);
-  if (threadIdx.x == 0) {
-    decide(c, st, a_, s);
-    st->ticket = 0u;
-  }
+  if (threadIdx.x < 32) decide(c, st, pr, a_, s);
+  if (threadIdx.x == 0) st->ticket = 0u;
 }
 
 // ------------------------------------------------------------------------------ adjoint

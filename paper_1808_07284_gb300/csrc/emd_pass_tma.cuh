@@ -1,0 +1,442 @@
+// The PDHG pass of emd_kernels.cuh (same three fused steps, same sums, same decision)
+// restructured for sm_103a's copy engine and issue rate:
+//
+//  * Persistent CTAs (two per SM) walk the tile list.  A producer warp stages each tile's
+//    six input planes (u^{k-1}, u^k as x and t, phi^{k-1}, f) by TMA (cp.async.bulk.tensor,
+//    one 3D descriptor per gather, zero fill outside the planes) into one of two shared
+//    memory stages; eight compute warps consume them.  Full / empty mbarriers per stage
+//    hand the stages over, so staging (descriptor and state loads, TMA issue) never
+//    holds up the compute warps, which synchronise among themselves on a named barrier.
+//  * A warp owns one staged row at a time and a lane owns four consecutive time samples
+//    (float4 shared-memory access); the j +- 1 neighbours at lane boundaries come from the
+//    adjacent lanes by warp shuffles, the i +- 1 neighbours from the rows above / below.
+//  * A CTA accumulates its sums over all its tiles of a gather and flushes them once
+//    (FP32 within the warp, FP64 above), adding its tile count to the gather's ticket;
+//    the CTA that completes the count takes the linesearch decision.
+//
+// Tile: TI receivers x 120 time samples; staged box (TI + 4) x 128 with the halo of 2
+// rows and 4 columns.  Lanes 1..30 own the 120 output columns; lanes 0 and 31 only
+// feed their neighbours.
+#pragma once
+
+#include "emd_kernels.cuh"
+
+namespace emd {
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// Arrive on the barrier and announce `bytes` of TMA traffic for the current phase.
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a barrier phase: false if it did not complete (the kernel then
+// reports EMD_ERR_TIMEOUT instead of spinning forever).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  for (int i = 0; i < (1 << 24); ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(map) : "memory");
+}
+
+// One box of a 3D tensor (x = time sample, y = receiver, z = plane) into shared memory.
+__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4 *>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Tile being staged / consumed in one shared-memory stage, with the per-gather scalars
+// the compute warps need (so they make no global loads of their own).
+struct StageInfo {
+  int gather, k, active, i0, j0, nr, nt, ntp;
+  int interior;  // every staged cell is inside the grid, away from its first/last row/column
+  int need_res;  // this pass's residual sums are read (a stopping test or the last iteration)
+  float alpha, coef, theta, inv, fmean, rdx, rdt;
+  float *ph_cur, *uxn, *utn;
+};
+
+template <int TI>
+struct TmaTile {
+  static constexpr int W = 128, TJ = 120, R = TI + 4;
+  static constexpr int BOX = R * W;      // floats of one staged plane
+  static constexpr int STAGE = 6 * BOX;  // floats of one stage
+  static constexpr unsigned BYTES = STAGE * 4u;
+  static constexpr size_t SMEM = 2u * STAGE * 4u + 128u;  // two stages + alignment slack
+};
+
+constexpr int kTmaThreads = kThreads + 32;  // eight compute warps + one producer warp
+
+// Producer: stage tile t (of any gather) into `dst`, announcing its bytes on `full`.
+// A tile of a gather that has already stopped is marked inactive (the barrier phase
+// still completes, with no traffic).
+template <int TI>
+__device__ __forceinline__ void stage_tile(const Ctl &c, int t, float *dst, uint64_t *full,
+                                           StageInfo &in) {
+  using T = TmaTile<TI>;
+  const int g = c.tile_shot[t];
+  const Shot &S = c.shots[g];
+  const State *st = c.states + g;
+  const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(st));
+  const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(st) + 1);
+  const int lt = t - S.tile0;
+  const int k = h0.x;
+  in.gather = g;
+  in.k = k;
+  in.active = !h0.y;
+  in.i0 = (lt / S.tiles_j) * TI;
+  in.j0 = (lt % S.tiles_j) * T::TJ;
+  in.nr = S.nr;
+  in.nt = S.nt;
+  in.ntp = S.ntp;
+  in.rdx = S.rdx;
+  in.rdt = S.rdt;
+  in.alpha = __int_as_float(h0.z);
+  in.coef = __int_as_float(h0.w);
+  in.theta = __int_as_float(h1.x);
+  in.inv = __int_as_float(h1.y);
+  in.fmean = __int_as_float(h1.z);
+  in.interior = in.i0 >= 3 && in.i0 + TI + 2 < S.nr && in.j0 >= 5 && in.j0 + 124 < S.nt;
+  in.need_res = (c.tol > 0.0 && (k + 1) % c.check_every == 0) || k + 1 >= c.max_iter;
+  in.ph_cur = S.ph[k & 1];
+  in.uxn = S.ux[(k + 1) % 3];
+  in.utn = S.ut[(k + 1) % 3];
+  if (!in.active) {
+    mbar_arrive_tx(full, 0u);
+    return;
+  }
+  const int kp = k == 0 ? 0 : (k - 1) % 3, kc = k % 3;
+  const int z[6] = {1 + 2 * kp, 2 + 2 * kp, 1 + 2 * kc, 2 + 2 * kc, 7 + ((k + 1) & 1), 0};
+  fence_proxy_async_smem();  // the stage was last written by ordinary stores
+  tmap_acquire(&S.tmap);
+  mbar_arrive_tx(full, T::BYTES);
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+    tma_load_3d(dst + a * T::BOX, &S.tmap, in.j0 - 4, in.i0 - 2, z[a], full);
+}
+
+// Compute warps: add the CTA's sums over `n` tiles of gather g to the gather's
+// accumulators; the CTA that completes the gather's tile count takes the decision.
+__device__ __forceinline__ void flush_gather(const Ctl &c, int g, int n, float (&v)[9]) {
+  const Shot &S = c.shots[g];
+  State *st = c.states + g;
+  double *acc = c.acc + static_cast<size_t>(g) * kSpread * kAcc;
+  block_accumulate<9, true>(v, acc + (blockIdx.x % kSpread) * kAcc);
+  __shared__ bool last;
+  __threadfence();
+  compute_sync<true>();
+  if (threadIdx.x == 0)
+    last = atomicAdd(&st->ticket, static_cast<unsigned>(n)) + n == static_cast<unsigned>(S.ntiles);
+  compute_sync<true>();
+  if (last) {
+    __threadfence();
+    DecidePrep pr;
+    if (threadIdx.x < 32) pr = decide_prep(c, st);
+    double a_[9];
+    gather_totals<9, true>(acc, a_);
+    if (threadIdx.x < 32) decide(c, st, pr, a_, g);
+    if (threadIdx.x == 0) st->ticket = 0u;
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) v[q] = 0.0f;
+}
+
+// The three fused steps of one PDHG iteration on one staged tile (see emd_kernels.cuh):
+// stage arrays UAx, UAt (u^{k-1}, then u^{k+1}), UBx, UBt (u^k), PH (phi^{k-1}, then
+// phi^k, then q), FF (f, then p); smem row r <-> receiver i0 - 2 + r, column c <->
+// time sample j0 - 4 + c.  Adds the tile's sums to v.  All compute threads.
+// INTERIOR: the tile is away from every edge of the grid, so no cell needs a boundary
+// mask (the masked instantiation gives the same values there).
+template <int TI, bool INTERIOR>
+__device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int lane, int warp,
+                                          float (&v)[9]) {
+  using T = TmaTile<TI>;
+  constexpr int W = T::W, R = T::R, BOX = T::BOX, NW = kThreads / 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  float *UAx = stg, *UAt = stg + BOX, *UBx = stg + 2 * BOX, *UBt = stg + 3 * BOX;
+  float *PH = stg + 4 * BOX, *FF = stg + 5 * BOX;
+  const int nr = in.nr, nt = in.nt, ntp = in.ntp;
+  const float rdx = in.rdx, rdt = in.rdt;
+  const float alpha = in.alpha, coef = in.coef, theta = in.theta, inv = in.inv, fmean = in.fmean;
+  const int i0 = in.i0;
+  const int gj0 = in.j0 - 4 + 4 * lane;  // time index of this lane's first cell
+  bool cin[4], ctl[4], ctr[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gj = gj0 + q;
+    cin[q] = INTERIOR || (gj >= 0 && gj < nt);
+    ctl[q] = INTERIOR || gj > 0;
+    ctr[q] = INTERIOR || gj + 1 < nt;
+  }
+  const bool need_res = in.need_res;
+  // lanes 1..30 own the tile's 120 output columns (inside the pitched row)
+  const bool own = lane >= 1 && lane <= 30 && gj0 < ntp;
+  float *ph_cur = in.ph_cur, *uxn = in.uxn, *utn = in.utn;
+
+  // ---- phase 1: phi^k = phi^{k-1} + c_k (p_{k-1} + theta_k q_{k-1}) on rows 0..R-2
+#pragma unroll
+  for (int rr = 0; rr < (R - 1 + NW - 1) / NW; ++rr) {
+    const int r = warp + NW * rr;
+    if (r >= R - 1) break;
+    const int gi = i0 - 2 + r;
+    const bool rin = INTERIOR || (gi >= 0 && gi < nr), xl = INTERIOR || gi > 0;
+    const bool xr = INTERIOR || gi + 1 < nr;
+    const int o = r * W + 4 * lane;
+    float bx[4], bxn[4], bt[4], ax[4], axn[4], at[4], ph[4], ff[4], res[4];
+    ld4(UBx + o, bx);
+    ld4(UBx + o + W, bxn);
+    ld4(UBt + o, bt);
+    ld4(UAx + o, ax);
+    ld4(UAx + o + W, axn);
+    ld4(UAt + o, at);
+    ld4(PH + o, ph);
+    ld4(FF + o, ff);
+    const float btN = __shfl_down_sync(FULL, bt[0], 1), atN = __shfl_down_sync(FULL, at[0], 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float bxl = xl ? bx[q] : 0.0f, bxr = xr ? bxn[q] : 0.0f;
+      const float axl = xl ? ax[q] : 0.0f, axr = xr ? axn[q] : 0.0f;
+      const float btl = ctl[q] ? bt[q] : 0.0f, btr = ctr[q] ? (q < 3 ? bt[q + 1] : btN) : 0.0f;
+      const float atl = ctl[q] ? at[q] : 0.0f, atr = ctr[q] ? (q < 3 ? at[q + 1] : atN) : 0.0f;
+      const float divB = (bxr - bxl) * rdx + (btr - btl) * rdt;
+      const float divA = (axr - axl) * rdx + (atr - atl) * rdt;
+      const float p = divB + (ff[q] - fmean);
+      const float qv = divB - divA;
+      const float phk = ph[q] + coef * (p + theta * qv);
+      res[q] = (rin && cin[q]) ? phk : 0.0f;
+    }
+    st4(PH + o, res);
+    if (own && r >= 2 && r < TI + 2 && gi < nr) st4(ph_cur + gi * ntp + gj0, res);
+  }
+  compute_sync<true>();
+
+  // ---- phase 2: u^{k+1} = shrink(u^k + alpha grad phi^k, alpha) / (1 + eps alpha), rows 1..R-2
+#pragma unroll
+  for (int rr = 0; rr < (R - 2 + NW - 1) / NW; ++rr) {
+    const int r = 1 + warp + NW * rr;
+    if (r >= R - 1) break;
+    const int gi = i0 - 2 + r;
+    const bool rin = INTERIOR || (gi >= 0 && gi < nr), xl = INTERIOR || gi > 0;
+    const int o = r * W + 4 * lane;
+    float ph[4], phu[4], bx[4], bt[4], nx[4], nv[4];
+    ld4(PH + o, ph);
+    ld4(PH + o - W, phu);
+    ld4(UBx + o, bx);
+    ld4(UBt + o, bt);
+    const float phL = __shfl_up_sync(FULL, ph[3], 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float gx = xl ? (ph[q] - phu[q]) * rdx : 0.0f;
+      const float gt = ctl[q] ? (ph[q] - (q == 0 ? phL : ph[q - 1])) * rdt : 0.0f;
+      const bool in_ = rin && cin[q];
+      nx[q] = in_ ? shrinkf(bx[q] + alpha * gx, alpha) * inv : 0.0f;
+      nv[q] = in_ ? shrinkf(bt[q] + alpha * gt, alpha) * inv : 0.0f;
+    }
+    st4(UAx + o, nx);
+    st4(UAt + o, nv);
+    if (own && r >= 2 && r < TI + 2 && gi < nr) {
+      st4(uxn + gi * ntp + gj0, nx);
+      st4(utn + gi * ntp + gj0, nv);
+    }
+  }
+  compute_sync<true>();
+
+  // ---- phase 3: p_k = div u^{k+1} + f -> FF, q_k = div(u^{k+1} - u^k) -> PH, rows 1..R-3
+#pragma unroll
+  for (int rr = 0; rr < (R - 3 + NW - 1) / NW; ++rr) {
+    const int r = 1 + warp + NW * rr;
+    if (r >= R - 2) break;
+    const int gi = i0 - 2 + r;
+    const bool rin = INTERIOR || (gi >= 0 && gi < nr), xl = INTERIOR || gi > 0;
+    const bool xr = INTERIOR || gi + 1 < nr;
+    const int o = r * W + 4 * lane;
+    float nx[4], nxn[4], nv[4], bx[4], bxn[4], bt[4], ff[4], pp[4], qq[4];
+    ld4(UAx + o, nx);
+    ld4(UAx + o + W, nxn);
+    ld4(UAt + o, nv);
+    ld4(UBx + o, bx);
+    ld4(UBx + o + W, bxn);
+    ld4(UBt + o, bt);
+    ld4(FF + o, ff);
+    const float nvN = __shfl_down_sync(FULL, nv[0], 1), btN = __shfl_down_sync(FULL, bt[0], 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float nxl = xl ? nx[q] : 0.0f, nxr = xr ? nxn[q] : 0.0f;
+      const float bxl = xl ? bx[q] : 0.0f, bxr = xr ? bxn[q] : 0.0f;
+      const float ntl = ctl[q] ? nv[q] : 0.0f, ntr = ctr[q] ? (q < 3 ? nv[q + 1] : nvN) : 0.0f;
+      const float btl = ctl[q] ? bt[q] : 0.0f, btr = ctr[q] ? (q < 3 ? bt[q + 1] : btN) : 0.0f;
+      const float divN = (nxr - nxl) * rdx + (ntr - ntl) * rdt;
+      const float divB = (bxr - bxl) * rdx + (btr - btl) * rdt;
+      const bool in_ = rin && cin[q];
+      pp[q] = in_ ? divN + (ff[q] - fmean) : 0.0f;
+      qq[q] = in_ ? divN - divB : 0.0f;
+    }
+    st4(FF + o, pp);
+    st4(PH + o, qq);
+  }
+  compute_sync<true>();
+
+  // ---- phase 4: the linesearch / residual / distance sums over the tile's own cells
+#pragma unroll
+  for (int rr = 0; rr < (TI + NW - 1) / NW; ++rr) {
+    const int r = 2 + warp + NW * rr;
+    if (r >= TI + 2) break;
+    const int gi = i0 - 2 + r;
+    const bool xl = INTERIOR || gi > 0;
+    const int o = r * W + 4 * lane;
+    float pp[4], pu[4], qq[4], qu[4], nx[4], nv[4], bx[4], bt[4];
+    ld4(FF + o, pp);
+    ld4(FF + o - W, pu);
+    ld4(PH + o, qq);
+    ld4(PH + o - W, qu);
+    ld4(UAx + o, nx);
+    ld4(UAt + o, nv);
+    ld4(UBx + o, bx);
+    ld4(UBt + o, bt);
+    const float pL = __shfl_up_sync(FULL, pp[3], 1), qL = __shfl_up_sync(FULL, qq[3], 1);
+    if (own && gi < nr) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!cin[q]) continue;
+        const float gpx = xl ? (pp[q] - pu[q]) * rdx : 0.0f;
+        const float gpt = ctl[q] ? (pp[q] - (q == 0 ? pL : pp[q - 1])) * rdt : 0.0f;
+        const float gqx = xl ? (qq[q] - qu[q]) * rdx : 0.0f;
+        const float gqt = ctl[q] ? (qq[q] - (q == 0 ? qL : qq[q - 1])) * rdt : 0.0f;
+        v[0] += pp[q] * pp[q];
+        v[1] += pp[q] * qq[q];
+        v[2] += qq[q] * qq[q];
+        v[3] += gpx * gpx + gpt * gpt;
+        v[4] += gpx * gqx + gpt * gqt;
+        v[5] += gqx * gqx + gqt * gqt;
+        if (need_res) {  // sum |u| is left to the finalize pass, which recomputes it
+          const float dx_ = nx[q] - bx[q], dt_ = nv[q] - bt[q];
+          v[7] += nx[q] * nx[q] + nv[q] * nv[q];
+          v[8] += dx_ * dx_ + dt_ * dt_;
+        }
+      }
+    }
+  }
+}
+
+// One PDHG pass over every gather's tiles.  Grid: persistent, at most two CTAs per SM;
+// CTA b takes tiles b, b + gridDim.x, ...  Warp 8 produces, warps 0..7 compute.
+template <int TI>
+__global__ void __launch_bounds__(kTmaThreads, 2) k_pass_tma(Ctl c, int total_tiles) {
+  using T = TmaTile<TI>;
+  extern __shared__ float4 dyn4[];
+  float *sbase = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(dyn4) + 127u) & ~static_cast<uintptr_t>(127u));
+  __shared__ __align__(8) uint64_t full[2], empty[2];
+  __shared__ StageInfo info[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kThreads / 32) {  // ---- producer warp: one lane stages every tile
+    if (lane == 0) {
+      int i = 0;
+      for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+        const int s = i & 1;
+        if (i >= 2 && !mbar_wait(&empty[s], ((i - 2) >> 1) & 1)) {
+          atomicExch(c.error, 1);
+          break;  // the compute warps time out on `full` in turn
+        }
+        stage_tile<TI>(c, t, sbase + s * T::STAGE, &full[s], info[s]);
+      }
+    }
+    return;
+  }
+
+  // ---- compute warps
+  float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int seg = 0;  // tiles of the current gather summed into v
+  int i = 0;
+  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+    const int s = i & 1;
+    const bool ok = mbar_wait(&full[s], (i >> 1) & 1);
+    int bad;
+    asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 p, %1, 0;\n"
+                 " bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(bad)
+                 : "r"(static_cast<unsigned>(ok)), "n"(kThreads)
+                 : "memory");
+    if (bad) {
+      if (threadIdx.x == 0) atomicExch(c.error, 1);
+      return;
+    }
+    const StageInfo in = info[s];
+    if (in.active) {
+      if (in.interior)
+        pass_tile<TI, true>(in, sbase + s * T::STAGE, lane, warp, v);
+      else
+        pass_tile<TI, false>(in, sbase + s * T::STAGE, lane, warp, v);
+      ++seg;
+      const int tn = t + gridDim.x;
+      const int gn = tn < total_tiles ? c.tile_shot[tn] : -1;
+      if (gn != in.gather) {
+        flush_gather(c, in.gather, seg, v);
+        seg = 0;
+      }
+    }
+    compute_sync<true>();                   // every compute warp is done with stage s
+    if (threadIdx.x == 0) mbar_arrive(&empty[s]);  // hand it back to the producer
+  }
+}
+}  // namespace emd

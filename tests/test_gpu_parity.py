@@ -147,7 +147,7 @@ def test_ragged_shapes(pkg, nr, nt):
     assert_parity(g, r)
 
 
-@pytest.mark.parametrize("tile", range(1, 7))
+@pytest.mark.parametrize("tile", range(1, 8))
 def test_every_tile_shape(pkg, tile):
     """Each compiled tile shape gives the oracle's iterates on a gather spanning several tiles."""
     obs, pred = synth.gather_pair_hyperbolic(nt=300, nr=37, seed=5)
