@@ -80,7 +80,10 @@ typedef struct {
   const float *phi_init; /* optional warm start for phi, device [nr][nt]; NULL = zeros   */
   const float *m_init;   /* optional warm start for u, device [2][nr][nt]; NULL = zeros  */
   int tile;          /* stencil tile-shape id (emd_tile_count() of them); 0 = automatic  */
-  int launch_mode;   /* 0: passes replayed from a captured CUDA graph; 1: plain launches */
+  int launch_mode;   /* 0: automatic -- every pass in one persistent cooperative launch when
+                        the TMA pass serves the gathers, else graph replays of the pass;
+                        1: one plain launch per pass; 2: one launch per pass, replayed
+                        from a captured CUDA graph                                       */
   int debug_fault;   /* fault injection for tests: 0 = off, 1 = every linesearch trial
                         fails (exercises EMD_ERR_LINESEARCH); never set in production   */
   double *trace;     /* optional per-iteration history, device, B x max_iter x 4 doubles

@@ -37,15 +37,16 @@ struct Shape {
   void (*iter)(Ctl);
   void (*fin)(Ctl);
   void (*iter_tma)(Ctl, int);
+  void (*solve_tma)(Ctl, int, int);  // every pass in one cooperative launch
 };
 
 #define EMD_SHAPE(TI, W) \
-  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr }
+  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr, nullptr }
 constexpr int kTmaTI = 13;
 const Shape kShapes[] = {EMD_SHAPE(16, 128), EMD_SHAPE(8, 128), EMD_SHAPE(32, 128),
                          EMD_SHAPE(8, 256),  EMD_SHAPE(16, 256), EMD_SHAPE(1, 256),
                          Shape{kTmaTI, 128, nullptr, emd::k_pass<kTmaTI, 128, true>,
-                               emd::k_pass_tma<kTmaTI>}};
+                               emd::k_pass_tma<kTmaTI>, emd::k_solve_tma<kTmaTI>}};
 #undef EMD_SHAPE
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kTmaShape = kNumShapes - 1;
@@ -144,7 +145,7 @@ bool params_ok(const emd_params &p) {
   if (p.ls_norm != 2) return false;  // the GPU path implements the Euclidean test only
   if (p.balance != EMD_BAL_NONE && p.balance != EMD_BAL_MEAN) return false;
   if (p.tile < 0 || p.tile > kNumShapes) return false;
-  if (p.launch_mode < 0 || p.launch_mode > 1) return false;
+  if (p.launch_mode < 0 || p.launch_mode > 2) return false;
   return true;
 }
 
@@ -181,7 +182,7 @@ class PassLauncher {
   }
   emd_status launch(int n, cudaStream_t stream) {
     int done = 0;
-    if (mode_ == 0 && n >= kChunk) {
+    if (mode_ != 1 && n >= kChunk) {
       if (!exec_ && capture() != EMD_OK) return EMD_ERR_CUDA;
       for (; done + kChunk <= n; done += kChunk) EMD_CK(cudaGraphLaunch(exec_, stream));
     }
@@ -346,8 +347,33 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   emd::k_prepare<<<dim3(std::min(nr_max, 128), B), kThreads, 0, stream>>>(ctl);
   EMD_CK(cudaGetLastError());
 
-  PassLauncher passes(sh, ctl, grid, p.launch_mode);
-  if (p.tol <= 0.0) {
+  // One cooperative launch for the whole solve, when the TMA pass is in use and every CTA
+  // of the grid can be resident at once (its CTAs wait on one another between passes).
+  bool persistent = false;
+  if (p.launch_mode == 0 && sh.solve_tma) {
+    int dev = 0, coop = 0, per_sm = 0;
+    const size_t tsmem = iter_smem_bytes(sh);
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+        cudaFuncSetAttribute(sh.solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(tsmem)) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sh.solve_tma, emd::kTmaThreads,
+                                                      tsmem) == cudaSuccess &&
+        per_sm >= 1) {
+      int tiles = grid, passes = p.max_iter;
+      const int cgrid = std::min(tiles, std::min(per_sm, 2) * sm_count());
+      Ctl cctl = ctl;
+      void *args[] = {&cctl, &tiles, &passes};
+      EMD_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(sh.solve_tma), dim3(cgrid),
+                                         dim3(emd::kTmaThreads), args, tsmem, stream));
+      persistent = true;
+    }
+    (void)cudaGetLastError();
+  }
+  PassLauncher passes(sh, ctl, grid, p.launch_mode == 1 ? 1 : 2);
+  if (persistent) {
+    // every pass already enqueued
+  } else if (p.tol <= 0.0) {
     const emd_status s = passes.launch(p.max_iter, stream);
     if (s != EMD_OK) return s;
   } else {

@@ -67,6 +67,8 @@ struct alignas(16) State {
   double mass_mu, mass_nu, imbalance;
   int trials;
   unsigned int ticket;
+  unsigned int tiles_done;          // persistent solve: tiles finished, cumulative over passes
+  unsigned int epoch;               // persistent solve: decisions taken (= next pass index)
 };
 
 constexpr int kSpread = 16;         // copies of each accumulator (spreads the atomics)

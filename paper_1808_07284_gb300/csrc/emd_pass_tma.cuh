@@ -54,12 +54,24 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait on a barrier phase: false if it did not complete (the kernel then
-// reports EMD_ERR_TIMEOUT instead of spinning forever).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Bound of every wait on another warp or CTA: a wait that outlasts it sets the solve's
+// error flag (EMD_ERR_TIMEOUT) and the kernel winds down instead of hanging.
+constexpr unsigned long long kSpinLimitNs = 4000000000ull;  // 4 s
+
+// Bounded wait on a barrier phase: false if it did not complete in time.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-  for (int i = 0; i < (1 << 24); ++i)
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned n = 0;; ++n) {
     if (mbar_test(bar, parity)) return true;
-  return false;
+    if ((n & 63u) == 63u && global_ns() - t0 > kSpinLimitNs) return false;
+  }
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -82,6 +94,35 @@ __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, 
       " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_acquire_int(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Waits until *counter >= target or the gather has stopped (*done != 0).  False on timeout.
+__device__ __forceinline__ bool wait_counter(const unsigned *counter, unsigned target,
+                                             const int *done) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned n = 0;; ++n) {
+    if (ld_acquire(counter) >= target || ld_acquire_int(done)) return true;
+    if ((n & 255u) == 255u && global_ns() - t0 > kSpinLimitNs) return false;
+    __nanosleep(64);
+  }
+}
+
+// Orders this thread's later TMA (async proxy) reads of global memory after the
+// ordinary stores of other CTAs that it has acquired.
+__device__ __forceinline__ void fence_proxy_async_all() {
+  asm volatile("fence.proxy.async;\n" ::: "memory");
 }
 
 __device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
@@ -120,9 +161,11 @@ constexpr int kTmaThreads = kThreads + 32;  // eight compute warps + one produce
 // Producer: stage tile t (of any gather) into `dst`, announcing its bytes on `full`.
 // A tile of a gather that has already stopped is marked inactive (the barrier phase
 // still completes, with no traffic).
+// kpass >= 0: the pass index of a persistent solve (the state's k may still lag it while
+// the previous decision is being taken); kpass < 0: use the state's k.
 template <int TI>
 __device__ __forceinline__ void stage_tile(const Ctl &c, int t, float *dst, uint64_t *full,
-                                           StageInfo &in) {
+                                           StageInfo &in, int kpass = -1) {
   using T = TmaTile<TI>;
   const int g = c.tile_shot[t];
   const Shot &S = c.shots[g];
@@ -130,7 +173,7 @@ __device__ __forceinline__ void stage_tile(const Ctl &c, int t, float *dst, uint
   const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(st));
   const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(st) + 1);
   const int lt = t - S.tile0;
-  const int k = h0.x;
+  const int k = kpass >= 0 ? kpass : h0.x;
   in.gather = g;
   in.k = k;
   in.active = !h0.y;
@@ -437,6 +480,192 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_pass_tma(Ctl c, int total_ti
     }
     compute_sync<true>();                   // every compute warp is done with stage s
     if (threadIdx.x == 0) mbar_arrive(&empty[s]);  // hand it back to the producer
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Persistent solve: every pass of the solve in one cooperative launch.
+//
+// Per gather, `tiles_done` counts finished tiles over all passes and `epoch` counts
+// decisions.  The CTA whose flush brings tiles_done to (k + 1) ntiles decides pass k
+// and then publishes epoch = k + 1.  The producer stages a tile of pass k once the
+// gather's pass k - 1 is complete (tiles_done >= k ntiles), which overlaps the first
+// tile's loads with the decision; the compute warps use the step sizes only after
+// epoch >= k.  At each pass boundary the compute warps tell the producer (mbarrier
+// `go`) whether any gather of this CTA is still running; the producer has staged the
+// pass's first tile before it knows, and the compute warps drain it when they stop.
+
+// Compute warps: add the CTA's sums over `n` tiles of gather g (pass k) to the gather's
+// accumulators; the CTA that completes the pass takes the decision and publishes it.
+__device__ __forceinline__ void flush_gather_persistent(const Ctl &c, int g, int n, int k,
+                                                        float (&v)[9]) {
+  const Shot &S = c.shots[g];
+  State *st = c.states + g;
+  double *acc = c.acc + static_cast<size_t>(g) * kSpread * kAcc;
+  block_accumulate<9, true>(v, acc + (blockIdx.x % kSpread) * kAcc);
+  __shared__ bool last;
+  __threadfence();
+  compute_sync<true>();
+  if (threadIdx.x == 0) {
+    const unsigned full_count = static_cast<unsigned>(k + 1) * static_cast<unsigned>(S.ntiles);
+    last = atomicAdd(&st->tiles_done, static_cast<unsigned>(n)) + n == full_count;
+  }
+  compute_sync<true>();
+  if (last) {
+    __threadfence();
+    DecidePrep pr;
+    if (threadIdx.x < 32) pr = decide_prep(c, st);
+    double a_[9];
+    gather_totals<9, true>(acc, a_);
+    if (threadIdx.x < 32) decide(c, st, pr, a_, g);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(&st->epoch, static_cast<unsigned>(k + 1));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) v[q] = 0.0f;
+}
+
+template <int TI>
+__global__ void __launch_bounds__(kTmaThreads, 2)
+    k_solve_tma(Ctl c, int total_tiles, int max_passes) {
+  using T = TmaTile<TI>;
+  extern __shared__ float4 dyn4[];
+  float *sbase = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(dyn4) + 127u) & ~static_cast<uintptr_t>(127u));
+  __shared__ __align__(8) uint64_t full[2], empty[2], gob;
+  __shared__ StageInfo info[2];
+  __shared__ int go_flag, hot_gather;
+  __shared__ float hot[5];  // alpha, coef, theta, 1/(1+eps alpha), fmean of hot_gather
+  __shared__ int hot_done;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
+    mbar_init(&gob, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kThreads / 32) {  // ---- producer warp: one lane stages every tile of every pass
+    if (lane == 0) {
+      int i = 0;
+      for (int k = 0; k < max_passes; ++k) {
+        bool first = true;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+          const int s = i & 1;
+          if (i >= 2 && !mbar_wait(&empty[s], ((i - 2) >> 1) & 1)) {
+            atomicExch(c.error, 1);
+            return;
+          }
+          const int g = c.tile_shot[t];
+          const State *st = c.states + g;
+          if (k > 0) {
+            const unsigned need = static_cast<unsigned>(k) * static_cast<unsigned>(c.shots[g].ntiles);
+            if (!wait_counter(&st->tiles_done, need, &st->done)) {
+              atomicExch(c.error, 1);
+              return;
+            }
+            fence_proxy_async_all();  // pass k - 1's stores, by other CTAs, feed these loads
+          }
+          stage_tile<TI>(c, t, sbase + s * T::STAGE, &full[s], info[s], k);
+          if (first) {
+            first = false;
+            if (!mbar_wait(&gob, k & 1)) {
+              atomicExch(c.error, 1);
+              return;
+            }
+            if (!go_flag) return;
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  // ---- compute warps
+  float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int i = 0;
+  for (int k = 0; k < max_passes; ++k) {
+    // pass boundary: is any gather of this CTA still running after decision k - 1?
+    if (threadIdx.x == 0) {
+      int go = 0;
+      bool ok = true;
+      int last_g = -1;
+      for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+        const int g = c.tile_shot[t];
+        if (g == last_g) continue;
+        last_g = g;
+        State *st = c.states + g;
+        ok = wait_counter(&st->epoch, static_cast<unsigned>(k), &st->done);
+        if (ok && !ld_acquire_int(&st->done)) go = 1;
+      }
+      if (!ok) atomicExch(c.error, 1);
+      go_flag = ok ? go : 0;
+      hot_gather = -1;
+      mbar_arrive(&gob);
+    }
+    compute_sync<true>();
+    if (!go_flag) {  // stop: drain the first tile the producer staged for this pass
+      (void)mbar_wait(&full[i & 1], (i >> 1) & 1);
+      return;
+    }
+    int seg = 0;  // tiles of the current gather summed into v
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+      const int s = i & 1;
+      const bool ok = mbar_wait(&full[s], (i >> 1) & 1);
+      int bad;
+      asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 p, %1, 0;\n"
+                   " bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+                   : "=r"(bad)
+                   : "r"(static_cast<unsigned>(ok)), "n"(kThreads)
+                   : "memory");
+      if (bad) {
+        if (threadIdx.x == 0) atomicExch(c.error, 1);
+        return;
+      }
+      StageInfo in = info[s];
+      if (in.gather != hot_gather) {  // this pass's step sizes of the tile's gather
+        compute_sync<true>();
+        if (threadIdx.x == 0) {
+          const State *st = c.states + in.gather;
+          const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(st));
+          const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(st) + 1);
+          hot_done = h0.y;
+          hot[0] = __int_as_float(h0.z);
+          hot[1] = __int_as_float(h0.w);
+          hot[2] = __int_as_float(h1.x);
+          hot[3] = __int_as_float(h1.y);
+          hot[4] = __int_as_float(h1.z);
+          hot_gather = in.gather;
+        }
+        compute_sync<true>();
+      }
+      if (!hot_done) {
+        in.alpha = hot[0];
+        in.coef = hot[1];
+        in.theta = hot[2];
+        in.inv = hot[3];
+        in.fmean = hot[4];
+        if (in.interior)
+          pass_tile<TI, true>(in, sbase + s * T::STAGE, lane, warp, v);
+        else
+          pass_tile<TI, false>(in, sbase + s * T::STAGE, lane, warp, v);
+        ++seg;
+        const int tn = t + gridDim.x;
+        const int gn = tn < total_tiles ? c.tile_shot[tn] : -1;
+        if (gn != in.gather) {
+          flush_gather_persistent(c, in.gather, seg, k, v);
+          seg = 0;
+        }
+      }
+      compute_sync<true>();                          // every compute warp is done with stage s
+      if (threadIdx.x == 0) mbar_arrive(&empty[s]);  // hand it back to the producer
+    }
   }
 }
 }  // namespace emd

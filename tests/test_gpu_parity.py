@@ -170,13 +170,24 @@ def test_no_balancing(pkg):
     assert_parity(g, r)
 
 
-def test_plain_launches_equal_graph_replays(pkg):
+@pytest.mark.parametrize("tol", [0.0, 1e-2])
+def test_launch_modes_agree(pkg, tol):
+    """One persistent launch (0), plain per-pass launches (1) and graph replays (2) run
+    the same iteration, with a fixed count and with a tolerance stop."""
     obs, pred = synth.gather_pair_hyperbolic(nt=200, nr=20, seed=6)
-    a = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=130, launch_mode=0)
-    b = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=130, launch_mode=1)
-    assert a["info"]["iters"] == b["info"]["iters"] == 130
-    assert a["dist"] == pytest.approx(b["dist"], rel=1e-9)
-    assert rel_l2(a["phi"], b["phi"]) <= 1e-6
+    dt, dx = (2e-3, 10.0) if tol == 0 else (1 / 199, 1 / 19)
+    runs = [gpu_solve(pkg, obs, pred, dt, dx, max_iter=130 if tol == 0 else 20000, tol=tol,
+                      launch_mode=m) for m in (0, 1, 2)]
+    for r in runs:
+        assert r["info"]["status"] == 0
+        assert r["info"]["iters"] == runs[0]["info"]["iters"]
+        assert r["info"]["ls_trials"] == runs[0]["info"]["ls_trials"]
+        assert r["dist"] == pytest.approx(runs[0]["dist"], rel=1e-9)
+        assert rel_l2(r["phi"], runs[0]["phi"]) <= 1e-6
+    if tol == 0:
+        assert runs[0]["info"]["iters"] == 130
+    else:
+        assert runs[0]["info"]["residual"] <= tol and runs[0]["info"]["iters"] < 20000
 
 
 def test_tolerance_stopping(pkg):
