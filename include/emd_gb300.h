@@ -110,6 +110,7 @@ typedef struct {
   int iters;          /* accepted PDHG iterations                                        */
   int ls_trials;      /* linesearch trials in total (>= iters)                           */
   int status;         /* emd_status of this solve                                        */
+  int launches;       /* kernel launches this solve made (a graph's nodes count one each) */
 } emd_result;
 
 /* Fills *p with the defaults listed above.  p must not be NULL. */

@@ -22,7 +22,7 @@ from ._binding import (  # noqa: F401
 )
 
 __all__ = [
-    "emd", "emd_batched", "emd_loss", "EMDFunction", "emd_decompose", "emd_dyn_solve",
+    "emd", "emd_batched", "emd_loss", "emd_loss_batched", "EMDFunction", "EMDBatchFunction", "emd_decompose", "emd_dyn_solve",
     "emd_dyn_solve_batched", "emd_dyn_solve_noalloc", "emd_adjoint", "emd_default_params", "emd_workspace_size",
     "emd_batched_workspace_size", "emd_status_string", "emd_tile_count", "EmdError",
 ]
@@ -92,18 +92,70 @@ def _autograd_function():
     return EMDFunction
 
 
+def _batched_autograd_function():
+    import torch
+
+    class EMDBatchFunction(torch.autograd.Function):
+        """dists[b] = EMD(f_pred[b], f_obs[b]) for B gathers solved together; backward
+        returns each gather's adjoint source from the phi kept by forward."""
+
+        @staticmethod
+        def forward(ctx, dts, dxs, params, *tensors):
+            B = len(tensors) // 2
+            preds = [t.detach().contiguous() for t in tensors[:B]]
+            obss = [t.detach().contiguous() for t in tensors[B:]]
+            dists, phis, _ms, infos = emd_batched(obss, preds, dts, dxs, **params)
+            ctx.save_for_backward(*phis)
+            ctx.dts, ctx.dxs = list(dts), list(dxs)
+            ctx.balance = params.get("balance", EMD_BAL_MEAN)
+            ctx.infos = infos
+            return torch.tensor(dists, dtype=torch.float32, device=preds[0].device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            phis = ctx.saved_tensors
+            B = len(phis)
+            g = grad_out.detach().to(torch.float32).contiguous()
+            gps, gos = [], []
+            for b, phi in enumerate(phis):
+                nr, nt = phi.shape
+                gp = torch.empty_like(phi)
+                go = torch.empty_like(phi)
+                ws = new_workspace(emd_workspace_size(nt, nr), phi.device)
+                emd_adjoint(phi, ctx.dts[b], ctx.dxs[b], ctx.balance, g[b:b + 1], gp, go, ws)
+                gps.append(gp)
+                gos.append(go)
+            return (None, None, None, *gps, *gos)
+
+    return EMDBatchFunction
+
+
 _EMDFunction = None
+_EMDBatchFunction = None
 
 
 def __getattr__(name):
-    global _EMDFunction
+    global _EMDFunction, _EMDBatchFunction
     if name == "EMDFunction":
         if _EMDFunction is None:
             _EMDFunction = _autograd_function()
         return _EMDFunction
+    if name == "EMDBatchFunction":
+        if _EMDBatchFunction is None:
+            _EMDBatchFunction = _batched_autograd_function()
+        return _EMDBatchFunction
     raise AttributeError(name)
 
 
 def emd_loss(f_pred, f_obs, dt, dx, **params):
     """Differentiable EMD misfit (a 0-dim float32 tensor) with the library's adjoint source."""
     return __getattr__("EMDFunction").apply(f_pred, f_obs, dt, dx, params)
+
+
+def emd_loss_batched(f_preds, f_obss, dts, dxs, **params):
+    """Differentiable EMD misfits of B gathers solved in one batched solve: a float32
+    tensor of B distances; backward gives each gather its adjoint source."""
+    B = len(f_preds)
+    dts = [float(v) for v in (dts if hasattr(dts, "__len__") else [dts] * B)]
+    dxs = [float(v) for v in (dxs if hasattr(dxs, "__len__") else [dxs] * B)]
+    return __getattr__("EMDBatchFunction").apply(dts, dxs, params, *f_preds, *f_obss)

@@ -180,7 +180,9 @@ class PassLauncher {
     if (exec_) cudaGraphExecDestroy(exec_);
     if (graph_) cudaGraphDestroy(graph_);
   }
+  int launched = 0;  // kernel launches so far (graph nodes included)
   emd_status launch(int n, cudaStream_t stream) {
+    launched += n;
     int done = 0;
     if (mode_ != 1 && n >= kChunk) {
       if (!exec_ && capture() != EMD_OK) return EMD_ERR_CUDA;
@@ -347,6 +349,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   emd::k_prepare<<<dim3(std::min(nr_max, 128), B), kThreads, 0, stream>>>(ctl);
   EMD_CK(cudaGetLastError());
 
+  int n_launch = 1;  // k_prepare
   // One cooperative launch for the whole solve, when the TMA pass is in use and every CTA
   // of the grid can be resident at once (its CTAs wait on one another between passes).
   bool persistent = false;
@@ -367,6 +370,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
       EMD_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(sh.solve_tma), dim3(cgrid),
                                          dim3(emd::kTmaThreads), args, tsmem, stream));
       persistent = true;
+      n_launch += 1;
     }
     (void)cudaGetLastError();
   }
@@ -394,6 +398,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
 
   sh.fin<<<grid, kThreads, smem, stream>>>(ctl);
   EMD_CK(cudaGetLastError());
+  n_launch += passes.launched + 1;
 
   std::vector<State> hs(B);
   int h_flags[2] = {0, 0};
@@ -427,6 +432,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     r.iters = st.k;
     r.ls_trials = st.trials;
     r.status = st.status;
+    r.launches = n_launch;
     if (first == EMD_OK && st.status != EMD_OK) first = static_cast<emd_status>(st.status);
   }
   return first;

@@ -125,6 +125,13 @@ __device__ __forceinline__ void fence_proxy_async_all() {
   asm volatile("fence.proxy.async;\n" ::: "memory");
 }
 
+// The contiguous run of tiles CTA b owns: [lo, hi) with lo = b T / G (T tiles, G CTAs).
+// Neighbouring tiles of a gather stay in one CTA (halo rows just staged are still in L2)
+// and a CTA meets as few gathers as possible (one flush per gather and pass).
+__device__ __forceinline__ int tile_lo(int b, int total, int grid) {
+  return static_cast<int>(static_cast<long long>(b) * total / grid);
+}
+
 __device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
   const float4 t = *reinterpret_cast<const float4 *>(p);
   v[0] = t.x;
@@ -412,7 +419,8 @@ __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int l
 }
 
 // One PDHG pass over every gather's tiles.  Grid: persistent, at most two CTAs per SM;
-// CTA b takes tiles b, b + gridDim.x, ...  Warp 8 produces, warps 0..7 compute.
+// CTA b takes the contiguous tiles [tile_lo(b), tile_lo(b + 1)).  Warp 8 produces,
+// warps 0..7 compute.
 template <int TI>
 __global__ void __launch_bounds__(kTmaThreads, 2) k_pass_tma(Ctl c, int total_tiles) {
   using T = TmaTile<TI>;
@@ -422,6 +430,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_pass_tma(Ctl c, int total_ti
   __shared__ __align__(8) uint64_t full[2], empty[2];
   __shared__ StageInfo info[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t_lo = tile_lo(blockIdx.x, total_tiles, gridDim.x);
+  const int t_hi = tile_lo(blockIdx.x + 1, total_tiles, gridDim.x);
 
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -435,7 +445,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_pass_tma(Ctl c, int total_ti
   if (warp == kThreads / 32) {  // ---- producer warp: one lane stages every tile
     if (lane == 0) {
       int i = 0;
-      for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+      for (int t = t_lo; t < t_hi; ++t, ++i) {
         const int s = i & 1;
         if (i >= 2 && !mbar_wait(&empty[s], ((i - 2) >> 1) & 1)) {
           atomicExch(c.error, 1);
@@ -451,7 +461,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_pass_tma(Ctl c, int total_ti
   float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int seg = 0;  // tiles of the current gather summed into v
   int i = 0;
-  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+  for (int t = t_lo; t < t_hi; ++t, ++i) {
     const int s = i & 1;
     const bool ok = mbar_wait(&full[s], (i >> 1) & 1);
     int bad;
@@ -471,8 +481,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_pass_tma(Ctl c, int total_ti
       else
         pass_tile<TI, false>(in, sbase + s * T::STAGE, lane, warp, v);
       ++seg;
-      const int tn = t + gridDim.x;
-      const int gn = tn < total_tiles ? c.tile_shot[tn] : -1;
+      const int tn = t + 1;
+      const int gn = tn < t_hi ? c.tile_shot[tn] : -1;
       if (gn != in.gather) {
         flush_gather(c, in.gather, seg, v);
         seg = 0;
@@ -540,6 +550,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
   __shared__ float hot[5];  // alpha, coef, theta, 1/(1+eps alpha), fmean of hot_gather
   __shared__ int hot_done;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t_lo = tile_lo(blockIdx.x, total_tiles, gridDim.x);
+  const int t_hi = tile_lo(blockIdx.x + 1, total_tiles, gridDim.x);
 
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -556,7 +568,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
       int i = 0;
       for (int k = 0; k < max_passes; ++k) {
         bool first = true;
-        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+        for (int t = t_lo; t < t_hi; ++t, ++i) {
           const int s = i & 1;
           if (i >= 2 && !mbar_wait(&empty[s], ((i - 2) >> 1) & 1)) {
             atomicExch(c.error, 1);
@@ -596,7 +608,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
       int go = 0;
       bool ok = true;
       int last_g = -1;
-      for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+      for (int t = t_lo; t < t_hi && ok; ++t) {
         const int g = c.tile_shot[t];
         if (g == last_g) continue;
         last_g = g;
@@ -615,7 +627,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
       return;
     }
     int seg = 0;  // tiles of the current gather summed into v
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+    for (int t = t_lo; t < t_hi; ++t, ++i) {
       const int s = i & 1;
       const bool ok = mbar_wait(&full[s], (i >> 1) & 1);
       int bad;
@@ -656,8 +668,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         else
           pass_tile<TI, false>(in, sbase + s * T::STAGE, lane, warp, v);
         ++seg;
-        const int tn = t + gridDim.x;
-        const int gn = tn < total_tiles ? c.tile_shot[tn] : -1;
+        const int tn = t + 1;
+        const int gn = tn < t_hi ? c.tile_shot[tn] : -1;
         if (gn != in.gather) {
           flush_gather_persistent(c, in.gather, seg, k, v);
           seg = 0;
