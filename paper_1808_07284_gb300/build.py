@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(LIB_DIR, "libemd_gb300.so")
 SOURCES = [os.path.join(HERE, "csrc", "emd_api.cu"), os.path.join(HERE, "csrc", "emd_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "emd_kernels.cuh"),
                   os.path.join(HERE, "csrc", "emd_pass_tma.cuh"),
+                  os.path.join(HERE, "csrc", "emd_resident.cuh"),
                   os.path.join(ROOT, "include", "emd_gb300.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -12,6 +12,7 @@
 #include "emd_gb300.h"
 #include "emd_kernels.cuh"
 #include "emd_pass_tma.cuh"
+#include "emd_resident.cuh"
 
 namespace {
 
@@ -350,10 +351,23 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   EMD_CK(cudaGetLastError());
 
   int n_launch = 1;  // k_prepare
+  // Small gathers: one CTA per gather keeps the whole solve in shared memory.
+  bool resident = p.launch_mode == 0 && p.tile == 0;
+  long long max_cells = 0;
+  for (int b = 0; b < B; ++b) max_cells = std::max(max_cells, static_cast<long long>(nt[b]) * nr[b]);
+  resident = resident && max_cells <= emd::kResidentMaxCells;
+  if (resident) {
+    const size_t rsmem = emd::resident_smem_bytes(max_cells);
+    EMD_CK(cudaFuncSetAttribute(emd::k_solve_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(rsmem)));
+    emd::k_solve_resident<<<B, emd::kResThreads, rsmem, stream>>>(ctl);
+    EMD_CK(cudaGetLastError());
+    n_launch += 1;
+  }
   // One cooperative launch for the whole solve, when the TMA pass is in use and every CTA
   // of the grid can be resident at once (its CTAs wait on one another between passes).
   bool persistent = false;
-  if (p.launch_mode == 0 && sh.solve_tma) {
+  if (!resident && p.launch_mode == 0 && sh.solve_tma) {
     int dev = 0, coop = 0, per_sm = 0;
     const size_t tsmem = iter_smem_bytes(sh);
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -375,7 +389,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     (void)cudaGetLastError();
   }
   PassLauncher passes(sh, ctl, grid, p.launch_mode == 1 ? 1 : 2);
-  if (persistent) {
+  if (persistent || resident) {
     // every pass already enqueued
   } else if (p.tol <= 0.0) {
     const emd_status s = passes.launch(p.max_iter, stream);

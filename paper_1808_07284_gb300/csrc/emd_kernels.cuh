@@ -225,29 +225,39 @@ __device__ __forceinline__ DecidePrep decide_prep(const Ctl &c, const State *st)
   return d;
 }
 
+// Outcome of one decision (identical in every lane of the deciding warp).
+struct Decision {
+  int status, trials_now, k_new;
+  bool done, checked;
+  double alpha, theta, coef, r_feas, r_step;
+};
+
 // Linesearch decision of Algorithm 1 from the sums of pass k, taken by one warp.
 // a: 0 P_pp, 1 P_pq, 2 P_qq, 3 G_pp, 4 G_pq, 5 G_qq, 6 sum|u|, 7 sum u^2, 8 sum du^2.
 // Trial t (0-based) uses a = alpha_k s_t with s_t = sqrt(1 + theta_k) xi^t, so the trials
 // do not depend on each other: lane t tests trial t (32 at a time) and a ballot picks the
-// first that passes -- the same choice as Algorithm 1's sequential backtracking.
-// Only lane 0 writes the state.
-__device__ void decide(const Ctl &c, State *st, const DecidePrep &d, const double (&a_)[9],
-                       int gather) {
+// first that passes -- the same choice as Algorithm 1's sequential backtracking.  Then the
+// stopping test (max_iter; the residual every check_every iterations when tol > 0).
+__device__ Decision decide_core(const Ctl &c, const DecidePrep &d, const double (&a_)[9]) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const double Ppp = a_[0], Ppq = a_[1], Pqq = a_[2], Gpp = a_[3], Gpq = a_[4], Gqq = a_[5];
   const bool finite = __all_sync(FULL, lane >= 9 || isfinite(a_[lane < 9 ? lane : 0]));
-  const int k0 = d.k;
-  bool done = false;
-  int trials_now = 1;
-  int status = ST_OK;
-  double alpha = d.alpha, theta = d.theta, coef = d.coef;
+  Decision o;
+  o.status = ST_OK;
+  o.trials_now = 1;
+  o.done = false;
+  o.checked = false;
+  o.alpha = d.alpha;
+  o.theta = d.theta;
+  o.coef = d.coef;
+  o.r_feas = o.r_step = -1.0;
   if (!finite) {
-    status = ST_NONFINITE;
-    done = true;
+    o.status = ST_NONFINITE;
+    o.done = true;
   } else if (c.linesearch) {
     const double z2 = c.zeta * c.zeta;
-    double s = d.s_lane, s2 = d.s_lane2, chunk2 = 1.0;
+    double s = d.s_lane, s2 = d.s_lane2;
     int found = -1;
     double s_found = 0.0;
     for (int t0 = 0; t0 < c.ls_max_trials && found < 0; t0 += 32) {
@@ -262,56 +272,70 @@ __device__ void decide(const Ctl &c, State *st, const DecidePrep &d, const doubl
         s_found = __shfl_sync(FULL, s, w);
       }
       s *= d.base32;
-      chunk2 = d.base32 * d.base32;
-      s2 *= chunk2;
+      s2 *= d.base32 * d.base32;
     }
     if (found >= 0) {
-      trials_now = found + 1;
-      theta = s_found;
-      alpha = d.alpha * s_found;
-      coef = c.delta * alpha;
+      o.trials_now = found + 1;
+      o.theta = s_found;
+      o.alpha = d.alpha * s_found;
+      o.coef = c.delta * o.alpha;
     } else {
-      trials_now = c.ls_max_trials;
-      status = ST_LINESEARCH;
-      done = true;
+      o.trials_now = c.ls_max_trials;
+      o.status = ST_LINESEARCH;
+      o.done = true;
     }
   } else {
-    coef = d.beta_fixed;
-    theta = 1.0;
+    o.coef = d.beta_fixed;
+    o.theta = 1.0;
   }
-  if (lane != 0) return;
-  st->s_p2 = Ppp;
+  o.k_new = o.status == ST_OK ? d.k + 1 : d.k;
+  if (!o.done && o.k_new >= c.max_iter) o.done = true;
+  if (!o.done && c.tol > 0.0 && o.k_new % c.check_every == 0) {
+    o.checked = true;
+    o.r_feas = d.fnorm > 0.0 ? sqrt(Ppp) / d.fnorm : sqrt(Ppp);
+    o.r_step = sqrt(a_[8]) / fmax(sqrt(a_[7]), 1e-30);
+    if (fmax(o.r_feas, o.r_step) <= c.tol) o.done = true;
+  }
+  return o;
+}
+
+// One entry of the optional per-iteration history (lane 0 of the deciding warp).
+__device__ __forceinline__ void write_trace(const Ctl &c, int gather, int k0, const Decision &o,
+                                            double Ppp, double fnorm) {
+  if (c.trace && k0 < c.max_iter) {
+    double *e = c.trace + (static_cast<size_t>(gather) * c.max_iter + k0) * 4;
+    e[0] = o.alpha;
+    e[1] = o.theta;
+    e[2] = static_cast<double>(o.trials_now);
+    e[3] = fnorm > 0.0 ? sqrt(Ppp) / fnorm : sqrt(Ppp);
+  }
+}
+
+// The decision of a gather whose state lives in global memory; only lane 0 writes it.
+__device__ void decide(const Ctl &c, State *st, const DecidePrep &d, const double (&a_)[9],
+                       int gather) {
+  const Decision o = decide_core(c, d, a_);
+  if ((threadIdx.x & 31) != 0) return;
+  st->s_p2 = a_[0];
   st->s_u1 = a_[6];
   st->s_u2 = a_[7];
   st->s_du2 = a_[8];
-  st->trials += trials_now;
-  if (status == ST_OK) {
-    st->alpha = alpha;
-    st->theta = theta;
-    st->coef = coef;
-    st->k = k0 + 1;
+  st->trials += o.trials_now;
+  if (o.status == ST_OK) {
+    st->alpha = o.alpha;
+    st->theta = o.theta;
+    st->coef = o.coef;
+    st->k = o.k_new;
     publish(st, c.eps);
   } else {
-    st->status = status;
+    st->status = o.status;
   }
-  if (c.trace && k0 < c.max_iter) {
-    double *e = c.trace + (static_cast<size_t>(gather) * c.max_iter + k0) * 4;
-    e[0] = alpha;
-    e[1] = theta;
-    e[2] = static_cast<double>(trials_now);
-    e[3] = d.fnorm > 0.0 ? sqrt(Ppp) / d.fnorm : sqrt(Ppp);
+  write_trace(c, gather, d.k, o, a_[0], d.fnorm);
+  if (o.checked) {
+    st->r_feas = o.r_feas;
+    st->r_step = o.r_step;
   }
-  const int k = status == ST_OK ? k0 + 1 : k0;
-  if (!done && k >= c.max_iter) done = true;
-  if (!done && c.tol > 0.0 && k % c.check_every == 0) {
-    const double fnorm = d.fnorm;
-    const double r_feas = fnorm > 0.0 ? sqrt(Ppp) / fnorm : sqrt(Ppp);
-    const double r_step = sqrt(a_[8]) / fmax(sqrt(a_[7]), 1e-30);
-    st->r_feas = r_feas;
-    st->r_step = r_step;
-    if (fmax(r_feas, r_step) <= c.tol) done = true;
-  }
-  if (done) {
+  if (o.done) {
     st->done = 1;
     atomicAdd(c.n_done, 1);
   }
