@@ -79,7 +79,12 @@ typedef struct {
   int balance;       /* emd_balance                                                      */
   const float *phi_init; /* optional warm start for phi, device [nr][nt]; NULL = zeros   */
   const float *m_init;   /* optional warm start for u, device [2][nr][nt]; NULL = zeros  */
-  int tile;          /* stencil tile-shape id (emd_tile_count() of them); 0 = automatic  */
+  int tile;          /* stencil tile-shape id (emd_tile_count() of them); 0 = automatic:
+                        gathers of <= 7168 cells are solved in shared memory (one CTA
+                        each, launch_mode 0), thin ones (<= 8 receivers) by the plain
+                        pass, the rest by the TMA pass in the tile shape an autotuner
+                        picks on the first solve of each (device, sizes) configuration
+                        (a few short timed trial solves, then cached per process)       */
   int launch_mode;   /* 0: automatic -- every pass in one persistent cooperative launch when
                         the TMA pass serves the gathers, else graph replays of the pass;
                         1: one plain launch per pass; 2: one launch per pass, replayed

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -39,24 +41,30 @@ struct Shape {
   void (*fin)(Ctl);
   void (*iter_tma)(Ctl, int);
   void (*solve_tma)(Ctl, int, int);  // every pass in one cooperative launch
+  int minb;                           // TMA pass: CTAs per SM it is compiled for
 };
 
 #define EMD_SHAPE(TI, W) \
-  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr, nullptr }
-constexpr int kTmaTI = 13;
-const Shape kShapes[] = {EMD_SHAPE(16, 128), EMD_SHAPE(8, 128), EMD_SHAPE(32, 128),
-                         EMD_SHAPE(8, 256),  EMD_SHAPE(16, 256), EMD_SHAPE(1, 256),
-                         Shape{kTmaTI, 128, nullptr, emd::k_pass<kTmaTI, 128, true>,
-                               emd::k_pass_tma<kTmaTI>, emd::k_solve_tma<kTmaTI>}};
+  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr, nullptr, 0 }
+#define EMD_TMA_SHAPE(TI, MINB)                                                             \
+  Shape {                                                                                   \
+    TI, 128, nullptr, emd::k_pass<TI, 128, true>, emd::k_pass_tma<TI, MINB>,                \
+        emd::k_solve_tma<TI, MINB>, MINB                                                    \
+  }
+const Shape kShapes[] = {EMD_SHAPE(16, 128),    EMD_SHAPE(8, 128),     EMD_SHAPE(32, 128),
+                         EMD_SHAPE(8, 256),     EMD_SHAPE(16, 256),    EMD_SHAPE(1, 256),
+                         EMD_TMA_SHAPE(13, 2),  EMD_TMA_SHAPE(8, 3),   EMD_TMA_SHAPE(21, 1)};
 #undef EMD_SHAPE
+#undef EMD_TMA_SHAPE
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
-constexpr int kTmaShape = kNumShapes - 1;
+constexpr int kTmaShape = 6;         // 13 x 120, two CTAs per SM: the untuned default
+constexpr int kTmaFirst = 6, kTmaLast = 8;
 
 // Dynamic shared memory of the plain pass / finalize pass of a shape, and of its
-// iteration pass.
+// iteration pass (two TMA stages of six (TI + 4) x 128 planes, plus alignment slack).
 size_t smem_bytes(const Shape &s) { return sizeof(float) * 6u * (s.ti + 4) * s.w; }
 size_t iter_smem_bytes(const Shape &s) {
-  return s.iter_tma ? emd::TmaTile<kTmaTI>::SMEM : smem_bytes(s);
+  return s.iter_tma ? 2u * 6u * (s.ti + 4) * 128u * sizeof(float) + 128u : smem_bytes(s);
 }
 
 // cuTensorMapEncodeTiled, reached through the runtime (no link against libcuda).
@@ -175,7 +183,7 @@ class PassLauncher {
   PassLauncher(const Shape &sh, const Ctl &ctl, int tiles, int mode)
       : sh_(sh), ctl_(ctl), tiles_(tiles), mode_(mode) {
     smem_ = iter_smem_bytes(sh);
-    grid_ = sh.iter_tma ? std::min(tiles, 2 * sm_count()) : tiles;
+    grid_ = sh.iter_tma ? std::min(tiles, sh.minb * sm_count()) : tiles;
   }
   ~PassLauncher() {
     if (exec_) cudaGraphExecDestroy(exec_);
@@ -227,16 +235,85 @@ class PassLauncher {
 
 // Fills S.tmap: the gather's nine planes as one 3D float tensor {ntp, nr, 9} with
 // strides (ntp * 4, plane bytes) and a box of (TI + 4) rows x 128 samples.
-bool encode_tmap(Shot &S, void *base, size_t plane_bytes) {
+bool encode_tmap(Shot &S, void *base, size_t plane_bytes, int rows) {
   EncodeTiled enc = encode_fn();
   if (!enc) return false;
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(S.ntp), static_cast<cuuint64_t>(S.nr), 9u};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(S.ntp) * 4u, plane_bytes};
-  const cuuint32_t box[3] = {128u, static_cast<cuuint32_t>(emd::TmaTile<kTmaTI>::R), 1u};
+  const cuuint32_t box[3] = {128u, static_cast<cuuint32_t>(rows), 1u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   return enc(&S.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
+                      const int *nr, const double *dt, const double *dx, const emd_params *pp,
+                      float *const *phi, float *const *m, emd_result *results, void *ws,
+                      size_t ws_bytes, cudaStream_t stream);
+
+// Tile-shape autotuner of the TMA pass.  The first default-tile solve of a (device,
+// gather sizes) configuration times each TMA shape on the caller's own data -- two short
+// fixed-iteration solves per shape, plain launches, whose difference is the per-pass
+// cost -- and keeps the fastest for the rest of the process.  The trial solves write
+// only the workspace and the outputs that the real solve then rewrites.
+std::mutex g_tune_lock;
+std::map<std::vector<long long>, int> g_tuned;
+
+int autotune_shape(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
+                   const int *nr, const double *dt, const double *dx, const emd_params &p,
+                   float *const *phi, float *const *m, emd_result *results, void *ws,
+                   size_t ws_bytes, cudaStream_t stream) {
+  int dev = 0;
+  (void)cudaGetDevice(&dev);
+  std::vector<long long> key = {dev, B};
+  for (int b = 0; b < B; ++b) {
+    key.push_back(nt[b]);
+    key.push_back(nr[b]);
+  }
+  std::lock_guard<std::mutex> guard(g_tune_lock);
+  auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) return it->second;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return kTmaShape;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return kTmaShape;
+  }
+  auto timed = [&](int shape, int iters) -> float {
+    emd_params q = p;
+    q.tile = shape + 1;
+    q.max_iter = iters;
+    q.tol = 0.0;
+    q.launch_mode = 1;
+    q.trace = nullptr;
+    if (cudaEventRecord(e0, stream) != cudaSuccess) return -1.0f;
+    if (solve_impl(B, f_obs, f_pred, nt, nr, dt, dx, &q, phi, m, results, ws, ws_bytes,
+                   stream) == EMD_ERR_CUDA)
+      return -1.0f;
+    float ms = -1.0f;
+    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return -1.0f;
+    return ms;
+  };
+  int best = kTmaShape;
+  float best_t = 0.0f;
+  for (int shape = kTmaFirst; shape <= kTmaLast; ++shape) {
+    (void)timed(shape, 4);  // first use: module load, attribute set-up
+    const float t1 = timed(shape, 8), t2 = timed(shape, 40);
+    if (t1 < 0.0f || t2 < 0.0f) continue;
+    const float per_pass = (t2 - t1) / 32.0f;
+    if (best_t == 0.0f || per_pass < best_t) {
+      best_t = per_pass;
+      best = shape;
+    }
+  }
+  (void)cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_tuned[key] = best;
+  return best;
 }
 
 emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
@@ -261,6 +338,12 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
 
   int si = pick_shape(p, B, nt, nr);
   if (kShapes[si].iter_tma && !encode_fn()) si = 0;  // no TMA descriptors: plain staging
+  long long max_cells = 0;
+  for (int b = 0; b < B; ++b) max_cells = std::max(max_cells, static_cast<long long>(nt[b]) * nr[b]);
+  // Small gathers: one CTA per gather keeps the whole solve in shared memory.
+  const bool resident = p.launch_mode == 0 && p.tile == 0 && max_cells <= emd::kResidentMaxCells;
+  if (p.tile == 0 && !resident && si == kTmaShape)
+    si = autotune_shape(B, f_obs, f_pred, nt, nr, dt, dx, p, phi, m, results, ws, ws_bytes, stream);
   const Shape &sh = kShapes[si];
   char *base = static_cast<char *>(ws);
 
@@ -288,7 +371,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     }
     S.ph[0] = reinterpret_cast<float *>(g + 7 * pl);
     S.ph[1] = reinterpret_cast<float *>(g + 8 * pl);
-    if (sh.iter_tma && !encode_tmap(S, g, pl)) return EMD_ERR_CUDA;
+    if (sh.iter_tma && !encode_tmap(S, g, pl, sh.ti + 4)) return EMD_ERR_CUDA;
     S.tiles_j = (nt[b] + (sh.w - 8) - 1) / (sh.w - 8);
     S.tile0 = static_cast<int>(tile_shot.size());
     S.ntiles = tiles_of(sh, nt[b], nr[b]);
@@ -351,11 +434,6 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   EMD_CK(cudaGetLastError());
 
   int n_launch = 1;  // k_prepare
-  // Small gathers: one CTA per gather keeps the whole solve in shared memory.
-  bool resident = p.launch_mode == 0 && p.tile == 0;
-  long long max_cells = 0;
-  for (int b = 0; b < B; ++b) max_cells = std::max(max_cells, static_cast<long long>(nt[b]) * nr[b]);
-  resident = resident && max_cells <= emd::kResidentMaxCells;
   if (resident) {
     const size_t rsmem = emd::resident_smem_bytes(max_cells);
     EMD_CK(cudaFuncSetAttribute(emd::k_solve_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -378,7 +456,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
                                                       tsmem) == cudaSuccess &&
         per_sm >= 1) {
       int tiles = grid, passes = p.max_iter;
-      const int cgrid = std::min(tiles, std::min(per_sm, 2) * sm_count());
+      const int cgrid = std::min(tiles, std::min(per_sm, sh.minb) * sm_count());
       Ctl cctl = ctl;
       void *args[] = {&cctl, &tiles, &passes};
       EMD_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(sh.solve_tma), dim3(cgrid),

@@ -421,8 +421,8 @@ __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int l
 // One PDHG pass over every gather's tiles.  Grid: persistent, at most two CTAs per SM;
 // CTA b takes the contiguous tiles [tile_lo(b), tile_lo(b + 1)).  Warp 8 produces,
 // warps 0..7 compute.
-template <int TI>
-__global__ void __launch_bounds__(kTmaThreads, 2) k_pass_tma(Ctl c, int total_tiles) {
+template <int TI, int MINB = 2>
+__global__ void __launch_bounds__(kTmaThreads, MINB) k_pass_tma(Ctl c, int total_tiles) {
   using T = TmaTile<TI>;
   extern __shared__ float4 dyn4[];
   float *sbase = reinterpret_cast<float *>(
@@ -537,8 +537,8 @@ __device__ __forceinline__ void flush_gather_persistent(const Ctl &c, int g, int
   for (int q = 0; q < 9; ++q) v[q] = 0.0f;
 }
 
-template <int TI>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+template <int TI, int MINB = 2>
+__global__ void __launch_bounds__(kTmaThreads, MINB)
     k_solve_tma(Ctl c, int total_tiles, int max_passes) {
   using T = TmaTile<TI>;
   extern __shared__ float4 dyn4[];

@@ -147,7 +147,7 @@ def test_ragged_shapes(pkg, nr, nt):
     assert_parity(g, r)
 
 
-@pytest.mark.parametrize("tile", range(1, 8))
+@pytest.mark.parametrize("tile", range(1, 10))
 def test_every_tile_shape(pkg, tile):
     """Each compiled tile shape gives the oracle's iterates on a gather spanning several tiles."""
     obs, pred = synth.gather_pair_hyperbolic(nt=300, nr=37, seed=5)
@@ -414,3 +414,34 @@ def test_marine_shots_sampled(pkg):
         g = dict(dist=d[b], phi=phis[b].double().cpu().numpy(), ux=ms[b][0].double().cpu().numpy(),
                  ut=ms[b][1].double().cpu().numpy(), info=infos[b])
         assert_parity(g, r, exact_trials=True)
+
+
+def test_1d_shift_sweep_61_shifts_batched(pkg):
+    """The 1D study in full: Ricker 8 Hz on [0, 1] (nt = 1024) against 61 shifted copies
+    (-0.3 .. 0.3 s), all 61 solved in one batch (one resident CTA per shift).  Every
+    distance matches the closed-form W1, and the misfit against the shift has a single
+    minimum at zero shift and grows with |shift| until the two signals stop overlapping,
+    where it flattens (the plateau of the discussion section)."""
+    dt, obs, preds = synth.shift_sweep_1d(nt=1024)
+    dev = torch.device("cuda:0")
+    O_ = [torch.from_numpy(obs).to(dev)] * len(preds)
+    P_ = [torch.from_numpy(p).to(dev) for _, p in preds]
+    d, phis, ms, infos = pkg.emd_batched(O_, P_, dt, 1.0, max_iter=100000)
+    shifts = np.array([s for s, _ in preds])
+    w = []
+    for (s, p), info in zip(preds, infos):
+        assert info["status"] == 0 and info["launches"] == 3
+        f = O.source_term(obs, p)[0]
+        w.append(O.w1_1d(np.maximum(f, 0), np.maximum(-f, 0), dt))
+    w = np.array(w)
+    l1 = np.array([i["dist_l1"] for i in infos])
+    nz = w > 0
+    assert np.max(np.abs(l1[nz] - w[nz]) / w[nz]) <= 2e-3
+    assert l1[np.argmin(np.abs(shifts))] <= 1e-6 * l1.max()
+    order = np.argsort(np.abs(shifts))
+    for side in (shifts > 0, shifts < 0):
+        idx = [i for i in order if side[i]]
+        vals = l1[idx]
+        assert np.all(np.diff(vals) >= -2e-3 * vals.max())  # non-decreasing in |shift|
+    far = np.abs(shifts) >= 0.2
+    assert np.ptp(l1[far]) <= 2e-3 * l1.max()  # plateau once the signals no longer overlap
