@@ -16,7 +16,12 @@ Contents:
   on the grid graph (Sec. 2.1, Eqs. for K(mu, nu) and OT(mu, nu)), solved with
   ``scipy.optimize.linprog``.
 
-Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (closed forms,
+* ``multigrid`` -- the two-grid strategy of Sec. 2.2 (closing paragraph) and Sec. 3.3:
+  restriction of both gathers in time, a coarse Algorithm 1 solve, sinc interpolation
+  of its solution onto the fine grid and a warm-started fine solve.
+
+Parity status: every function is pinned by ``tests/test_oracle_pins.py`` and
+``tests/test_oracle_mg_pins.py`` (closed forms,
 library routines, exact LPs, invariants, hand-worked fixtures).  The fixed-iteration PDHG
 trajectory has no closed form; it is pinned step by step (each step checked against the
 defining minimisation / test of the paper) and at convergence by the LPs and the 1D

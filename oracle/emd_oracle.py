@@ -23,7 +23,8 @@ listed with its reason in the design notes of the repository):
 * Q7  balance=MEAN subtracts the mean of f = Pcal - Pobs; balance=NONE solves as printed.
 * Q8  gradient of the returned distance w.r.t. Pcal is dx dt (phi - mean phi) (MEAN) or
        dx dt phi (NONE); w.r.t. Pobs it is the negative.
-* Q10 u^0 = 0 and phi^0 = 0 unless a warm start is given.
+* Q10 u^0 = 0 and phi^0 = 0 unless a warm start is given; a warm start's outer faces
+       (x flux of receiver 0, time flux of sample 0) are set to zero (Q1).
 * Q11 nr = 1 means a 1D problem: no x component, lambda = 4/dt^2, cell area dt.
 * Q12 the backtracking gives up after ``ls_max_trials`` trials (status LINESEARCH).
 * Q13 ``iters`` counts accepted outer iterations; trials are counted separately.
@@ -246,6 +247,8 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
     if p.m_init is not None:
         ux = np.array(p.m_init[0], np.float64)
         ut = np.array(p.m_init[1], np.float64)
+        ux[0, :] = 0.0  # Q1: the outer faces carry no flux, whatever the warm start holds
+        ut[:, 0] = 0.0
     else:
         ux = np.zeros((nr, nt))
         ut = np.zeros((nr, nt))
