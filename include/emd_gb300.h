@@ -205,6 +205,89 @@ emd_status emd_dyn_solve_noalloc(const float *f_obs, const float *f_pred, int nt
                                  double dt, double dx, const emd_params *params, float *phi,
                                  float *m, emd_result *result, emd_stream_t stream);
 
+/*
+ * Two-grid solve (Sec. 2.2, closing paragraph; Sec. 3.3).  The paper speeds up large
+ * gathers by solving the EMD on a resampled, coarser gather, building the primal variable
+ * on the original grid by sinc interpolation and running the primal-dual method on the
+ * fine grid from there (Sec. 3.3: time resampled 3000 -> 301 samples, 150 coarse
+ * iterations).  Readings fixed here:
+ *  - the coarse grid coarsens the time axis only, by the integer `factor` r: coarse
+ *    sample J of a row is the mean of fine samples rJ .. rJ + r - 1 (record padded with
+ *    zeros to a multiple of r, so the mass is kept), coarse spacing r*dt, same dx;
+ *  - sinc interpolation is the Whittaker-Shannon sum over every coarse sample of the
+ *    record, at fine positions (j - (r-1)/2)/r (cell-centred: phi, x flux) or j/r (time
+ *    flux, which sits on the faces between time cells), in coarse-sample units; the
+ *    outer faces (x flux of receiver 0, time flux of sample 0) are zero;
+ *  - phi is interpolated along with u unless interpolate_phi = 0 (then the fine solve
+ *    starts from phi = 0, the paper's sentence read literally).
+ */
+typedef struct {
+  int factor;          /* time coarsening r >= 1 (1 = a coarse solve on the fine grid)    */
+  int coarse_max_iter; /* cap on the coarse solve's accepted iterations (>= 1)            */
+  double coarse_tol;   /* the coarse solve's stopping residual; 0 = run coarse_max_iter   */
+  int interpolate_phi; /* 1: phi is interpolated too (default); 0: fine phi starts at 0  */
+} emd_mg_params;
+
+/* Fills *p: factor = 10, coarse_max_iter = 150, coarse_tol = 0 (the Sec. 3.3 setting),
+ * interpolate_phi = 1.  p must not be NULL. */
+void emd_default_mg_params(emd_mg_params *p);
+
+/* Bytes of workspace emd_dyn_solve_mg needs (0 if invalid, e.g. ceil(nt/factor) < 2).
+ * Never less than emd_workspace_size(nt, nr). */
+size_t emd_mg_workspace_size(int nt, int nr, int factor);
+
+/* The same for emd_dyn_solve_batched_mg over B gathers (host size arrays). */
+size_t emd_batched_mg_workspace_size(int B, const int *nt, const int *nr, int factor);
+
+/*
+ * Time restriction, the first step of the two-grid solve: out[i][J] = (1/r) *
+ * sum_{j = rJ}^{min(rJ + r, nt) - 1} in[i][j] for J < ceil(nt / r).  in: device [nr][nt],
+ * out: device [nr][ceil(nt / r)], FP32 (summed in FP32, in order of j).  r >= 1.
+ * Does not synchronise.
+ */
+emd_status emd_restrict_time(const float *in, int nt, int nr, int factor, float *out,
+                             emd_stream_t stream);
+
+/*
+ * Sinc interpolation, the third step of the two-grid solve: out[i][j] = sum_J in[i][J]
+ * sinc(x_j - J), J < nc, j < nt, with x_j = j / r when staggered = 1 (time faces) and
+ * (j - (r - 1)/2) / r when staggered = 0 (cell centres).  zero_row0 / zero_col0 = 1 write
+ * 0 to row 0 / column 0 (outer faces).  in: device [nr][nc], out: device [nr][nt], FP32
+ * accumulation.  Does not synchronise.
+ */
+emd_status emd_prolong_time(const float *in, int nc, int nr, int factor, int nt, int staggered,
+                            int zero_row0, int zero_col0, float *out, emd_stream_t stream);
+
+/*
+ * Two-grid EMD solve: restriction of f_obs and f_pred, a coarse Algorithm 1 solve (params
+ * with max_iter = coarse_max_iter and tol = coarse_tol, no trace), sinc interpolation of
+ * its phi and u into the output arrays phi and m, and the fine Algorithm 1 solve with
+ * params, warm-started from there.  Arguments are those of emd_dyn_solve, plus mg (host,
+ * NULL = defaults) and coarse (HOST, nullable: the coarse solve's result, on the coarse
+ * grid).  params->phi_init and params->m_init must be NULL (the warm start is the coarse
+ * solution).  result describes the fine solve; result->launches counts every launch of
+ * the call.  Workspace: emd_mg_workspace_size(nt, nr, mg->factor) bytes.  A coarse solve
+ * that fails returns its status without the fine solve.  Synchronises `stream`.
+ */
+emd_status emd_dyn_solve_mg(const float *f_obs, const float *f_pred, int nt, int nr, double dt,
+                            double dx, const emd_params *params, const emd_mg_params *mg,
+                            float *phi, float *m, emd_result *result, emd_result *coarse,
+                            void *workspace, size_t ws_bytes, emd_stream_t stream);
+
+/*
+ * Batched two-grid solve: both stages of every gather run as one batched solve each (one
+ * restriction and one interpolation launch for all gathers).  Arguments are those of
+ * emd_dyn_solve_batched plus mg and coarse (HOST array of B, nullable).  Workspace:
+ * emd_batched_mg_workspace_size(B, nt, nr, mg->factor) bytes.
+ */
+emd_status emd_dyn_solve_batched_mg(int B, const float *const *f_obs,
+                                    const float *const *f_pred, const int *nt, const int *nr,
+                                    const double *dt, const double *dx,
+                                    const emd_params *params, const emd_mg_params *mg,
+                                    float *const *phi, float *const *m, emd_result *results,
+                                    emd_result *coarse, void *workspace, size_t ws_bytes,
+                                    emd_stream_t stream);
+
 /* Static, human-readable name of a status code. */
 const char *emd_status_string(emd_status s);
 

@@ -16,37 +16,54 @@ from __future__ import annotations
 from ._binding import (  # noqa: F401
     EMD_BAL_MEAN, EMD_BAL_NONE, EMD_ERR_ARG, EMD_ERR_CUDA, EMD_ERR_LINESEARCH,
     EMD_ERR_NONFINITE, EMD_ERR_TIMEOUT, EMD_ERR_WORKSPACE, EMD_OK, EXPORTS,
-    EmdError, EmdParams, EmdResult, emd_adjoint, emd_batched_workspace_size, emd_decompose,
-    emd_default_params, emd_dyn_solve, emd_dyn_solve_batched, emd_dyn_solve_noalloc, emd_status_string,
-    emd_tile_count, emd_workspace_size, lib, new_workspace,
+    EmdError, EmdMgParams, EmdParams, EmdResult, emd_adjoint, emd_batched_mg_workspace_size,
+    emd_batched_workspace_size, emd_decompose, emd_default_mg_params, emd_default_params,
+    emd_dyn_solve, emd_dyn_solve_batched, emd_dyn_solve_batched_mg, emd_dyn_solve_mg,
+    emd_dyn_solve_noalloc, emd_mg_workspace_size, emd_prolong_time, emd_restrict_time,
+    emd_status_string, emd_tile_count, emd_workspace_size, lib, new_workspace,
 )
 
 __all__ = [
     "emd", "emd_batched", "emd_loss", "emd_loss_batched", "EMDFunction", "EMDBatchFunction", "emd_decompose", "emd_dyn_solve",
     "emd_dyn_solve_batched", "emd_dyn_solve_noalloc", "emd_adjoint", "emd_default_params", "emd_workspace_size",
     "emd_batched_workspace_size", "emd_status_string", "emd_tile_count", "EmdError",
+    "emd_dyn_solve_mg", "emd_dyn_solve_batched_mg", "emd_default_mg_params", "emd_mg_workspace_size",
+    "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time",
 ]
 
 
-def emd(f_obs, f_pred, dt, dx, workspace=None, stream=None, check=True, **params):
+def emd(f_obs, f_pred, dt, dx, workspace=None, stream=None, check=True, multigrid=None, **params):
     """One EMD solve.  Returns ``(dist, phi[nr, nt], m[2, nr, nt], info)``.
 
     ``params`` are ``emd_params`` fields (eps, xi, zeta, delta, alpha0, tol, max_iter,
     check_every, ls_max_trials, linesearch, balance, phi_init, m_init, tile, launch_mode).
+    ``multigrid``: None for one solve, or a dict of ``emd_mg_params`` fields (factor,
+    coarse_max_iter, coarse_tol, interpolate_phi; ``{}`` = the Sec. 3.3 setting) for the
+    two-grid solve of Sec. 2.2/3.3; ``info["coarse"]`` then describes the coarse solve.
     """
     import torch
     nr, nt = f_obs.shape
     p = emd_default_params(**params)
     phi = torch.empty((nr, nt), dtype=torch.float32, device=f_obs.device)
     m = torch.empty((2, nr, nt), dtype=torch.float32, device=f_obs.device)
+    if multigrid is not None:
+        g = emd_default_mg_params(**multigrid)
+        ws = workspace if workspace is not None else new_workspace(
+            emd_mg_workspace_size(nt, nr, g.factor), f_obs.device)
+        res, cres = emd_dyn_solve_mg(f_obs, f_pred, float(dt), float(dx), p, g, phi, m, ws, stream,
+                                     check=check)
+        info = res.as_dict()
+        info["coarse"] = cres.as_dict()
+        return res.dist, phi, m, info
     ws = workspace if workspace is not None else new_workspace(emd_workspace_size(nt, nr), f_obs.device)
     res = emd_dyn_solve(f_obs, f_pred, float(dt), float(dx), p, phi, m, ws, stream, check=check)
     return res.dist, phi, m, res.as_dict()
 
 
-def emd_batched(f_obs, f_pred, dts, dxs, workspace=None, stream=None, check=True, **params):
+def emd_batched(f_obs, f_pred, dts, dxs, workspace=None, stream=None, check=True, multigrid=None,
+                **params):
     """B independent solves in one launch per iteration.  Lists in, lists out:
-    ``(dists, phis, ms, infos)``."""
+    ``(dists, phis, ms, infos)``.  ``multigrid`` as for :func:`emd` (both stages batched)."""
     import torch
     B = len(f_obs)
     dts = [float(v) for v in (dts if hasattr(dts, "__len__") else [dts] * B)]
@@ -55,6 +72,16 @@ def emd_batched(f_obs, f_pred, dts, dxs, workspace=None, stream=None, check=True
     phis = [torch.empty_like(t) for t in f_obs]
     ms = [torch.empty((2,) + tuple(t.shape), dtype=torch.float32, device=t.device) for t in f_obs]
     nts, nrs = [int(t.shape[1]) for t in f_obs], [int(t.shape[0]) for t in f_obs]
+    if multigrid is not None:
+        g = emd_default_mg_params(**multigrid)
+        ws = workspace if workspace is not None else new_workspace(
+            emd_batched_mg_workspace_size(nts, nrs, g.factor), f_obs[0].device)
+        res, cres = emd_dyn_solve_batched_mg(f_obs, f_pred, dts, dxs, p, g, phis, ms, ws, stream,
+                                             check=check)
+        infos = [r.as_dict() for r in res]
+        for i, c in zip(infos, cres):
+            i["coarse"] = c.as_dict()
+        return [r.dist for r in res], phis, ms, infos
     ws = workspace if workspace is not None else new_workspace(
         emd_batched_workspace_size(nts, nrs), f_obs[0].device)
     res = emd_dyn_solve_batched(f_obs, f_pred, dts, dxs, p, phis, ms, ws, stream, check=check)

@@ -20,7 +20,9 @@ EMD_BAL_NONE, EMD_BAL_MEAN = 0, 1
 EXPORTS = (
     "emd_default_params", "emd_tile_count", "emd_workspace_size", "emd_decompose",
     "emd_dyn_solve", "emd_batched_workspace_size", "emd_dyn_solve_batched", "emd_adjoint",
-    "emd_status_string", "emd_dyn_solve_noalloc",
+    "emd_status_string", "emd_dyn_solve_noalloc", "emd_default_mg_params", "emd_mg_workspace_size",
+    "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time", "emd_dyn_solve_mg",
+    "emd_dyn_solve_batched_mg",
 )
 
 
@@ -35,6 +37,15 @@ class EmdParams(ctypes.Structure):
         ("phi_init", c_void_p), ("m_init", c_void_p),
         ("tile", c_int), ("launch_mode", c_int), ("debug_fault", c_int),
         ("trace", c_void_p),
+    ]
+
+
+class EmdMgParams(ctypes.Structure):
+    """Mirror of ``emd_mg_params``."""
+
+    _fields_ = [
+        ("factor", c_int), ("coarse_max_iter", c_int), ("coarse_tol", c_double),
+        ("interpolate_phi", c_int),
     ]
 
 
@@ -96,6 +107,27 @@ def lib() -> ctypes.CDLL:
         L.emd_dyn_solve_noalloc.argtypes = [c_void_p, c_void_p, c_int, c_int, c_double, c_double,
                                             P(EmdParams), c_void_p, c_void_p, P(EmdResult), c_void_p]
         L.emd_dyn_solve_noalloc.restype = c_int
+        L.emd_default_mg_params.argtypes = [P(EmdMgParams)]
+        L.emd_default_mg_params.restype = None
+        L.emd_mg_workspace_size.argtypes = [c_int, c_int, c_int]
+        L.emd_mg_workspace_size.restype = c_size_t
+        L.emd_batched_mg_workspace_size.argtypes = [c_int, P(c_int), P(c_int), c_int]
+        L.emd_batched_mg_workspace_size.restype = c_size_t
+        L.emd_restrict_time.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]
+        L.emd_restrict_time.restype = c_int
+        L.emd_prolong_time.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_int,
+                                       c_void_p, c_void_p]
+        L.emd_prolong_time.restype = c_int
+        L.emd_dyn_solve_mg.argtypes = [c_void_p, c_void_p, c_int, c_int, c_double, c_double,
+                                       P(EmdParams), P(EmdMgParams), c_void_p, c_void_p,
+                                       P(EmdResult), P(EmdResult), c_void_p, c_size_t, c_void_p]
+        L.emd_dyn_solve_mg.restype = c_int
+        L.emd_dyn_solve_batched_mg.argtypes = [c_int, P(c_void_p), P(c_void_p), P(c_int), P(c_int),
+                                               P(c_double), P(c_double), P(EmdParams),
+                                               P(EmdMgParams), P(c_void_p), P(c_void_p),
+                                               P(EmdResult), P(EmdResult), c_void_p, c_size_t,
+                                               c_void_p]
+        L.emd_dyn_solve_batched_mg.restype = c_int
         L.emd_status_string.argtypes = [c_int]
         L.emd_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -133,6 +165,25 @@ def emd_default_params(**overrides) -> EmdParams:
             v = _ptr(v)
         setattr(p, k, v)
     return p
+
+
+def emd_default_mg_params(**overrides) -> EmdMgParams:
+    g = EmdMgParams()
+    lib().emd_default_mg_params(ctypes.byref(g))
+    for k, v in overrides.items():
+        if not hasattr(g, k):
+            raise TypeError(f"unknown two-grid parameter {k}")
+        setattr(g, k, v)
+    return g
+
+
+def emd_mg_workspace_size(nt: int, nr: int, factor: int) -> int:
+    return lib().emd_mg_workspace_size(nt, nr, factor)
+
+
+def emd_batched_mg_workspace_size(nts, nrs, factor: int) -> int:
+    B = len(nts)
+    return lib().emd_batched_mg_workspace_size(B, (c_int * B)(*nts), (c_int * B)(*nrs), factor)
 
 
 def emd_tile_count() -> int:
@@ -242,3 +293,66 @@ def emd_dyn_solve_noalloc(f_obs, f_pred, dt, dx, params: EmdParams, phi, m, stre
     if check and st != EMD_OK:
         raise EmdError(st, "emd_dyn_solve_noalloc")
     return res
+
+
+def emd_restrict_time(x, factor: int, out, stream=None):
+    """Time restriction of a [nr, nt] gather into out [nr, ceil(nt / factor)] (block means)."""
+    nr, nt = x.shape
+    _check_grid(x, nr, nt, "in")
+    _check_grid(out, nr, -(-nt // factor), "out")
+    st = lib().emd_restrict_time(_ptr(x), nt, nr, factor, _ptr(out), _stream(stream))
+    if st != EMD_OK:
+        raise EmdError(st, "emd_restrict_time")
+
+
+def emd_prolong_time(x, factor: int, out, staggered: bool, zero_row0=False, zero_col0=False,
+                     stream=None):
+    """Sinc interpolation of coarse rows x [nr, nc] onto out [nr, nt]."""
+    nr, nc = x.shape
+    nt = int(out.shape[-1])
+    _check_grid(x, nr, nc, "in")
+    _check_grid(out, nr, nt, "out")
+    st = lib().emd_prolong_time(_ptr(x), nc, nr, factor, nt, int(staggered), int(zero_row0),
+                                int(zero_col0), _ptr(out), _stream(stream))
+    if st != EMD_OK:
+        raise EmdError(st, "emd_prolong_time")
+
+
+def emd_dyn_solve_mg(f_obs, f_pred, dt, dx, params: EmdParams, mg: EmdMgParams, phi, m, workspace,
+                     stream=None, check: bool = True):
+    """Two-grid solve through the C ABI; returns (fine EmdResult, coarse EmdResult)."""
+    nr, nt = f_obs.shape
+    _check_grid(f_obs, nr, nt, "f_obs")
+    _check_grid(f_pred, nr, nt, "f_pred")
+    _check_grid(phi, nr, nt, "phi")
+    _check_grid(m, nr, nt, "m", planes=2)
+    res, cres = EmdResult(), EmdResult()
+    st = lib().emd_dyn_solve_mg(_ptr(f_obs), _ptr(f_pred), nt, nr, dt, dx, ctypes.byref(params),
+                                ctypes.byref(mg), _ptr(phi), _ptr(m), ctypes.byref(res),
+                                ctypes.byref(cres), _ptr(workspace), workspace.numel(),
+                                _stream(stream))
+    if check and st != EMD_OK:
+        raise EmdError(st, "emd_dyn_solve_mg")
+    return res, cres
+
+
+def emd_dyn_solve_batched_mg(f_obs, f_pred, dts, dxs, params: EmdParams, mg: EmdMgParams, phis, ms,
+                             workspace, stream=None, check: bool = True):
+    """B two-grid solves through the C ABI; returns (fine results, coarse results)."""
+    B = len(f_obs)
+    nts, nrs = [int(t.shape[1]) for t in f_obs], [int(t.shape[0]) for t in f_obs]
+    for b in range(B):
+        _check_grid(f_obs[b], nrs[b], nts[b], f"f_obs[{b}]")
+        _check_grid(f_pred[b], nrs[b], nts[b], f"f_pred[{b}]")
+        _check_grid(phis[b], nrs[b], nts[b], f"phi[{b}]")
+        _check_grid(ms[b], nrs[b], nts[b], f"m[{b}]", planes=2)
+    P = c_void_p * B
+    res, cres = (EmdResult * B)(), (EmdResult * B)()
+    st = lib().emd_dyn_solve_batched_mg(
+        B, P(*[_ptr(t) for t in f_obs]), P(*[_ptr(t) for t in f_pred]), (c_int * B)(*nts),
+        (c_int * B)(*nrs), (c_double * B)(*dts), (c_double * B)(*dxs), ctypes.byref(params),
+        ctypes.byref(mg), P(*[_ptr(t) for t in phis]), P(*[_ptr(t) for t in ms]), res, cres,
+        _ptr(workspace), workspace.numel(), _stream(stream))
+    if check and st != EMD_OK:
+        raise EmdError(st, "emd_dyn_solve_batched_mg")
+    return list(res), list(cres)

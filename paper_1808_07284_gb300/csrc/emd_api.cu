@@ -13,6 +13,7 @@
 
 #include "emd_gb300.h"
 #include "emd_kernels.cuh"
+#include "emd_multigrid.cuh"
 #include "emd_pass_tma.cuh"
 #include "emd_resident.cuh"
 
@@ -247,23 +248,34 @@ bool encode_tmap(Shot &S, void *base, size_t plane_bytes, int rows) {
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// What a solve takes besides the public arguments: per-gather warm starts (the two-grid
+// solve hands each gather its interpolated coarse solution; NULL arrays fall back to
+// params' single warm start) and whether to run the finalize pass.  Without it nothing
+// but the workspace is written -- the autotuner's trial solves must not touch phi and m,
+// which may hold the warm start they read.
+struct SolveExtra {
+  const float *const *phi_init = nullptr;
+  const float *const *m_init = nullptr;
+  bool finalize = true;
+};
+
 emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
                       const int *nr, const double *dt, const double *dx, const emd_params *pp,
                       float *const *phi, float *const *m, emd_result *results, void *ws,
-                      size_t ws_bytes, cudaStream_t stream);
+                      size_t ws_bytes, cudaStream_t stream, const SolveExtra &x = SolveExtra{});
 
 // Tile-shape autotuner of the TMA pass.  The first default-tile solve of a (device,
 // gather sizes) configuration times each TMA shape on the caller's own data -- two short
 // fixed-iteration solves per shape, plain launches, whose difference is the per-pass
-// cost -- and keeps the fastest for the rest of the process.  The trial solves write
-// only the workspace and the outputs that the real solve then rewrites.
+// cost -- and keeps the fastest for the rest of the process.  The trial solves stop
+// before the finalize pass, so they write the workspace only.
 std::mutex g_tune_lock;
 std::map<std::vector<long long>, int> g_tuned;
 
 int autotune_shape(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
                    const int *nr, const double *dt, const double *dx, const emd_params &p,
                    float *const *phi, float *const *m, emd_result *results, void *ws,
-                   size_t ws_bytes, cudaStream_t stream) {
+                   size_t ws_bytes, cudaStream_t stream, const SolveExtra &x) {
   int dev = 0;
   (void)cudaGetDevice(&dev);
   std::vector<long long> key = {dev, B};
@@ -288,8 +300,10 @@ int autotune_shape(int B, const float *const *f_obs, const float *const *f_pred,
     q.launch_mode = 1;
     q.trace = nullptr;
     if (cudaEventRecord(e0, stream) != cudaSuccess) return -1.0f;
-    if (solve_impl(B, f_obs, f_pred, nt, nr, dt, dx, &q, phi, m, results, ws, ws_bytes,
-                   stream) == EMD_ERR_CUDA)
+    SolveExtra trial = x;
+    trial.finalize = false;
+    if (solve_impl(B, f_obs, f_pred, nt, nr, dt, dx, &q, phi, m, results, ws, ws_bytes, stream,
+                   trial) == EMD_ERR_CUDA)
       return -1.0f;
     float ms = -1.0f;
     if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -319,7 +333,7 @@ int autotune_shape(int B, const float *const *f_obs, const float *const *f_pred,
 emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
                       const int *nr, const double *dt, const double *dx, const emd_params *pp,
                       float *const *phi, float *const *m, emd_result *results, void *ws,
-                      size_t ws_bytes, cudaStream_t stream) {
+                      size_t ws_bytes, cudaStream_t stream, const SolveExtra &x) {
   emd_params p;
   emd_default_params(&p);
   if (pp) p = *pp;
@@ -343,7 +357,8 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   // Small gathers: one CTA per gather keeps the whole solve in shared memory.
   const bool resident = p.launch_mode == 0 && p.tile == 0 && max_cells <= emd::kResidentMaxCells;
   if (p.tile == 0 && !resident && si == kTmaShape)
-    si = autotune_shape(B, f_obs, f_pred, nt, nr, dt, dx, p, phi, m, results, ws, ws_bytes, stream);
+    si = autotune_shape(B, f_obs, f_pred, nt, nr, dt, dx, p, phi, m, results, ws, ws_bytes, stream,
+                        x);
   const Shape &sh = kShapes[si];
   char *base = static_cast<char *>(ws);
 
@@ -357,8 +372,8 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     S.p_pred = f_pred[b];
     S.phi_out = phi[b];
     S.m_out = m[b];
-    S.phi_init = p.phi_init;
-    S.m_init = p.m_init;
+    S.phi_init = x.phi_init ? x.phi_init[b] : p.phi_init;
+    S.m_init = x.m_init ? x.m_init[b] : p.m_init;
     S.nt = nt[b];
     S.nr = nr[b];
     S.ntp = ntp_of(nt[b]);
@@ -488,6 +503,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     }
   }
 
+  if (!x.finalize) return EMD_OK;  // an autotuner trial: the caller times the stream
   sh.fin<<<grid, kThreads, smem, stream>>>(ctl);
   EMD_CK(cudaGetLastError());
   n_launch += passes.launched + 1;
@@ -528,6 +544,161 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     if (first == EMD_OK && st.status != EMD_OK) first = static_cast<emd_status>(st.status);
   }
   return first;
+}
+
+// ---------------------------------------------------------------- two-grid solve
+
+int coarse_nt(int nt, int r) { return (nt + r - 1) / r; }
+
+bool mg_ok(const emd_mg_params &g) {
+  return g.factor >= 1 && g.factor <= (1 << 16) && g.coarse_max_iter >= 1 &&
+         std::isfinite(g.coarse_tol) && g.coarse_tol >= 0.0 &&
+         (g.interpolate_phi == 0 || g.interpolate_phi == 1);
+}
+
+// Workspace of the two-grid solve: the coarse solve's workspace, then per gather the
+// coarse gathers (obs, pred), the coarse solution (phi, m) and the job table.  The fine
+// solve reuses the buffer from offset 0 once the interpolation has read the coarse
+// solution (stream order), so the total is the larger of the two stages.
+struct MgLayout {
+  bool ok = false;
+  size_t coarse_ws = 0, jobs = 0, total = 0;
+  std::vector<int> ntc;
+  std::vector<size_t> obs, pred, phi, m;
+};
+
+constexpr int kMaxMgGathers = 65535 / 3;  // interpolation jobs ride on gridDim.z
+
+MgLayout mg_layout(int B, const int *nt, const int *nr, int r) {
+  MgLayout M;
+  if (B < 1 || B > kMaxMgGathers || r < 1) return M;
+  for (int b = 0; b < B; ++b) {
+    if (!size_ok(nt[b], nr[b])) return M;
+    M.ntc.push_back(coarse_nt(nt[b], r));
+    if (!size_ok(M.ntc[b], nr[b])) return M;  // fewer than two coarse samples
+  }
+  const Layout Lc = layout(B, M.ntc.data(), nr);
+  M.coarse_ws = Lc.total;
+  size_t off = align256(Lc.total);
+  for (int b = 0; b < B; ++b) {
+    const size_t n = sizeof(float) * static_cast<size_t>(nr[b]) * M.ntc[b];
+    M.obs.push_back(off);
+    off += align256(n);
+    M.pred.push_back(off);
+    off += align256(n);
+    M.phi.push_back(off);
+    off += align256(n);
+    M.m.push_back(off);
+    off += align256(2 * n);
+  }
+  M.jobs = off;
+  off += align256(sizeof(emd::TimeJob) * 3u * B);
+  M.total = std::max(off, layout(B, nt, nr).total);
+  M.ok = true;
+  return M;
+}
+
+emd_status mg_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
+                   const int *nr, const double *dt, const double *dx, const emd_params *pp,
+                   const emd_mg_params *gp, float *const *phi, float *const *m,
+                   emd_result *results, emd_result *coarse, void *ws, size_t ws_bytes,
+                   cudaStream_t stream) {
+  emd_params p;
+  emd_default_params(&p);
+  if (pp) p = *pp;
+  emd_mg_params g;
+  emd_default_mg_params(&g);
+  if (gp) g = *gp;
+  if (B < 1 || !f_obs || !f_pred || !nt || !nr || !dt || !dx || !phi || !m || !results)
+    return EMD_ERR_ARG;
+  if (!params_ok(p) || !mg_ok(g) || p.phi_init || p.m_init) return EMD_ERR_ARG;
+  for (int b = 0; b < B; ++b) {
+    if (!f_obs[b] || !f_pred[b] || !phi[b] || !m[b]) return EMD_ERR_ARG;
+    if (!(dt[b] > 0) || !std::isfinite(dt[b]) || !(dx[b] > 0) || !std::isfinite(dx[b]))
+      return EMD_ERR_ARG;
+  }
+  const MgLayout M = mg_layout(B, nt, nr, g.factor);
+  if (!M.ok) return EMD_ERR_ARG;
+  if (!ws || !aligned256(ws) || ws_bytes < M.total) return EMD_ERR_WORKSPACE;
+  char *base = static_cast<char *>(ws);
+  const int r = g.factor;
+
+  // 1. restriction of both gathers (one launch for every gather)
+  std::vector<const float *> obs_c(B), pred_c(B);
+  std::vector<float *> phi_c(B), m_c(B);
+  std::vector<double> dt_c(B);
+  std::vector<emd::TimeJob> jobs;
+  long long cells_c = 0;
+  for (int b = 0; b < B; ++b) {
+    float *o = reinterpret_cast<float *>(base + M.obs[b]);
+    float *q = reinterpret_cast<float *>(base + M.pred[b]);
+    obs_c[b] = o;
+    pred_c[b] = q;
+    phi_c[b] = reinterpret_cast<float *>(base + M.phi[b]);
+    m_c[b] = reinterpret_cast<float *>(base + M.m[b]);
+    dt_c[b] = dt[b] * r;
+    jobs.push_back({f_obs[b], o, nr[b], nt[b], M.ntc[b], r, 0, 0, 0});
+    jobs.push_back({f_pred[b], q, nr[b], nt[b], M.ntc[b], r, 0, 0, 0});
+    cells_c = std::max(cells_c, static_cast<long long>(nr[b]) * M.ntc[b]);
+  }
+  emd::TimeJob *djobs = reinterpret_cast<emd::TimeJob *>(base + M.jobs);
+  EMD_CK(cudaMemcpyAsync(djobs, jobs.data(), sizeof(emd::TimeJob) * jobs.size(),
+                         cudaMemcpyHostToDevice, stream));
+  const int rgrid = static_cast<int>(
+      std::min<long long>((cells_c + emd::kRestrictThreads - 1) / emd::kRestrictThreads, 4096));
+  emd::k_restrict_time<<<dim3(rgrid, static_cast<unsigned>(jobs.size())), emd::kRestrictThreads,
+                         0, stream>>>(djobs, emd::TimeJob{});
+  EMD_CK(cudaGetLastError());
+
+  // 2. the coarse solve (Algorithm 1 on the coarse grids, spacing r dt)
+  emd_params q = p;
+  q.max_iter = g.coarse_max_iter;
+  q.tol = g.coarse_tol;
+  q.trace = nullptr;
+  std::vector<emd_result> cres(B);
+  const emd_status cs = solve_impl(B, obs_c.data(), pred_c.data(), M.ntc.data(), nr, dt_c.data(),
+                                   dx, &q, phi_c.data(), m_c.data(), cres.data(), ws, M.coarse_ws,
+                                   stream);
+  if (coarse)
+    for (int b = 0; b < B; ++b) coarse[b] = cres[b];
+  if (cs != EMD_OK) {
+    for (int b = 0; b < B; ++b) {
+      std::memset(&results[b], 0, sizeof(emd_result));
+      results[b].status = cres[b].status != EMD_OK ? cres[b].status : cs;
+      results[b].launches = cres[b].launches + 1;
+    }
+    return cs;
+  }
+
+  // 3. sinc interpolation of the coarse solution into phi and m (one launch)
+  jobs.clear();
+  int nt_max = 0, nr_max = 0;
+  for (int b = 0; b < B; ++b) {
+    const size_t nc = static_cast<size_t>(nr[b]) * M.ntc[b];
+    const size_t nf = static_cast<size_t>(nr[b]) * nt[b];
+    if (g.interpolate_phi) jobs.push_back({phi_c[b], phi[b], nr[b], M.ntc[b], nt[b], r, 0, 0, 0});
+    jobs.push_back({m_c[b], m[b], nr[b], M.ntc[b], nt[b], r, 0, 1, 0});
+    jobs.push_back({m_c[b] + nc, m[b] + nf, nr[b], M.ntc[b], nt[b], r, 1, 0, 1});
+    nt_max = std::max(nt_max, nt[b]);
+    nr_max = std::max(nr_max, nr[b]);
+  }
+  EMD_CK(cudaMemcpyAsync(djobs, jobs.data(), sizeof(emd::TimeJob) * jobs.size(),
+                         cudaMemcpyHostToDevice, stream));
+  const dim3 pgrid((nt_max + emd::kIpBN - 1) / emd::kIpBN, (nr_max + emd::kIpBM - 1) / emd::kIpBM,
+                   static_cast<unsigned>(jobs.size()));
+  emd::k_prolong_time<<<pgrid, emd::kIpThreads, 0, stream>>>(djobs, emd::TimeJob{});
+  EMD_CK(cudaGetLastError());
+
+  // 4. the fine solve, warm-started from phi and m in place (its prepare pass copies them
+  //    into the workspace before anything writes phi or m again)
+  std::vector<const float *> phi_init(phi, phi + B), m_init(m, m + B);
+  SolveExtra x;
+  x.phi_init = g.interpolate_phi ? phi_init.data() : nullptr;
+  x.m_init = m_init.data();
+  const emd_status fs = solve_impl(B, f_obs, f_pred, nt, nr, dt, dx, &p, phi, m, results, ws,
+                                   ws_bytes, stream, x);
+  for (int b = 0; b < B; ++b) results[b].launches += cres[b].launches + 2;
+  return fs;
 }
 
 }  // namespace
@@ -635,6 +806,72 @@ emd_status emd_adjoint(const float *phi, int nt, int nr, double dt, double dx, i
                                                      grad_pred, grad_obs);
   EMD_CK(cudaGetLastError());
   return EMD_OK;
+}
+
+void emd_default_mg_params(emd_mg_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->factor = 10;
+  p->coarse_max_iter = 150;
+  p->coarse_tol = 0.0;
+  p->interpolate_phi = 1;
+}
+
+size_t emd_mg_workspace_size(int nt, int nr, int factor) {
+  const MgLayout M = mg_layout(1, &nt, &nr, factor);
+  return M.ok ? M.total : 0;
+}
+
+size_t emd_batched_mg_workspace_size(int B, const int *nt, const int *nr, int factor) {
+  if (B < 1 || !nt || !nr) return 0;
+  const MgLayout M = mg_layout(B, nt, nr, factor);
+  return M.ok ? M.total : 0;
+}
+
+emd_status emd_restrict_time(const float *in, int nt, int nr, int factor, float *out,
+                             emd_stream_t stream) {
+  if (!in || !out || factor < 1 || factor > (1 << 16) || !size_ok(nt, nr)) return EMD_ERR_ARG;
+  const int nc = coarse_nt(nt, factor);
+  const long long cells = static_cast<long long>(nr) * nc;
+  const int grid = static_cast<int>(
+      std::min<long long>((cells + emd::kRestrictThreads - 1) / emd::kRestrictThreads, 4096));
+  emd::k_restrict_time<<<dim3(grid, 1), emd::kRestrictThreads, 0,
+                         reinterpret_cast<cudaStream_t>(stream)>>>(
+      nullptr, emd::TimeJob{in, out, nr, nt, nc, factor, 0, 0, 0});
+  EMD_CK(cudaGetLastError());
+  return EMD_OK;
+}
+
+emd_status emd_prolong_time(const float *in, int nc, int nr, int factor, int nt, int staggered,
+                            int zero_row0, int zero_col0, float *out, emd_stream_t stream) {
+  if (!in || !out || factor < 1 || factor > (1 << 16) || nc < 1 || nt < 1) return EMD_ERR_ARG;
+  if (!size_ok(std::max(nt, 2), nr) || !size_ok(std::max(nc, 2), nr)) return EMD_ERR_ARG;
+  if (static_cast<long long>(factor) * nc > (1ll << 28)) return EMD_ERR_ARG;  // 2 r J fits an int
+  if ((staggered | zero_row0 | zero_col0) & ~1) return EMD_ERR_ARG;
+  const dim3 grid((nt + emd::kIpBN - 1) / emd::kIpBN, (nr + emd::kIpBM - 1) / emd::kIpBM, 1);
+  emd::k_prolong_time<<<grid, emd::kIpThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      nullptr, emd::TimeJob{in, out, nr, nc, nt, factor, staggered, zero_row0, zero_col0});
+  EMD_CK(cudaGetLastError());
+  return EMD_OK;
+}
+
+emd_status emd_dyn_solve_mg(const float *f_obs, const float *f_pred, int nt, int nr, double dt,
+                            double dx, const emd_params *params, const emd_mg_params *mg,
+                            float *phi, float *m, emd_result *result, emd_result *coarse,
+                            void *workspace, size_t ws_bytes, emd_stream_t stream) {
+  return mg_impl(1, &f_obs, &f_pred, &nt, &nr, &dt, &dx, params, mg, &phi, &m, result, coarse,
+                 workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+emd_status emd_dyn_solve_batched_mg(int B, const float *const *f_obs,
+                                    const float *const *f_pred, const int *nt, const int *nr,
+                                    const double *dt, const double *dx,
+                                    const emd_params *params, const emd_mg_params *mg,
+                                    float *const *phi, float *const *m, emd_result *results,
+                                    emd_result *coarse, void *workspace, size_t ws_bytes,
+                                    emd_stream_t stream) {
+  return mg_impl(B, f_obs, f_pred, nt, nr, dt, dx, params, mg, phi, m, results, coarse,
+                 workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 const char *emd_status_string(emd_status s) {

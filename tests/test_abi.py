@@ -43,24 +43,28 @@ def test_struct_layout_matches_header(B, tmp_path):
     probe = tmp_path / "probe.c"
     fields_p = [f for f, _ in B.EmdParams._fields_]
     fields_r = [f for f, _ in B.EmdResult._fields_]
+    fields_g = [f for f, _ in B.EmdMgParams._fields_]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "emd_gb300.h"', "int main(void){"]
-    lines.append('printf("%zu %zu\\n", sizeof(emd_params), sizeof(emd_result));')
+    lines.append('printf("%zu %zu %zu\\n", sizeof(emd_params), sizeof(emd_result), sizeof(emd_mg_params));')
     for f in fields_p:
         lines.append(f'printf("p {f} %zu\\n", offsetof(emd_params, {f}));')
     for f in fields_r:
         lines.append(f'printf("r {f} %zu\\n", offsetof(emd_result, {f}));')
+    for f in fields_g:
+        lines.append(f'printf("g {f} %zu\\n", offsetof(emd_mg_params, {f}));')
     lines.append("return 0;}")
     probe.write_text("\n".join(lines))
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(probe), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
-    sp, sr = map(int, out[0].split())
+    sp, sr, sg = map(int, out[0].split())
     assert sp == ctypes.sizeof(B.EmdParams) and sr == ctypes.sizeof(B.EmdResult)
+    assert sg == ctypes.sizeof(B.EmdMgParams)
     for line in out[1:]:
         if not line:
             continue
         kind, name, off = line.split()
-        cls = B.EmdParams if kind == "p" else B.EmdResult
+        cls = {"p": B.EmdParams, "r": B.EmdResult, "g": B.EmdMgParams}[kind]
         assert getattr(cls, name).offset == int(off), name
 
 
@@ -108,6 +112,45 @@ def test_argument_errors_need_no_gpu(B):
     assert L.emd_adjoint(fake, 8, 4, 1e-3, 10.0, 3, None, fake, None, fake, 1 << 20, None) == B.EMD_ERR_ARG
     assert L.emd_decompose(fake, None, 8, 4, 1e-3, 10.0, None, None, None, fake, 1 << 20, None) == B.EMD_ERR_ARG
     assert B.emd_status_string(B.EMD_ERR_LINESEARCH) == "linesearch did not terminate"
+
+
+def test_two_grid_defaults_sizes_and_argument_errors(B):
+    """Sec. 3.3 defaults; the two-grid workspace covers the fine solve; bad arguments are
+    refused before any CUDA call."""
+    g = B.emd_default_mg_params()
+    assert (g.factor, g.coarse_max_iter, g.coarse_tol, g.interpolate_phi) == (10, 150, 0.0, 1)
+    for f in (1, 2, 10, 1499):
+        assert B.emd_mg_workspace_size(3000, 400, f) >= B.emd_workspace_size(3000, 400)
+    assert B.emd_mg_workspace_size(3000, 400, 2999) > 0  # two coarse samples: the least there can be
+    assert B.emd_mg_workspace_size(3000, 400, 3000) == 0
+    assert B.emd_mg_workspace_size(3000, 400, 0) == 0
+    assert B.emd_batched_mg_workspace_size([100, 200], [3, 4], 4) >= B.emd_batched_workspace_size([100, 200], [3, 4])
+    L = B.lib()
+    res, cres = B.EmdResult(), B.EmdResult()
+    fake = ctypes.c_void_p(256)
+    p = B.emd_default_params()
+    ok = B.emd_default_mg_params(factor=4)
+    big = 1 << 30
+
+    def call(prm, mg, ws=fake, nbytes=big, nt=64, nr=4):
+        return L.emd_dyn_solve_mg(fake, fake, nt, nr, 1e-3, 10.0, ctypes.byref(prm), ctypes.byref(mg), fake,
+                                  fake, ctypes.byref(res), ctypes.byref(cres), ws, nbytes, None)
+
+    for bad in [dict(factor=0), dict(coarse_max_iter=0), dict(coarse_tol=-1.0), dict(interpolate_phi=2),
+                dict(factor=64)]:  # 64 samples by 64: one coarse sample
+        mg = B.emd_default_mg_params(**{"factor": 4, **bad})
+        assert call(p, mg, nbytes=16) == B.EMD_ERR_ARG, bad
+    assert call(p, B.emd_default_mg_params(factor=63), nbytes=16) == B.EMD_ERR_WORKSPACE
+    warm = B.emd_default_params()
+    warm.phi_init = 256
+    assert call(warm, ok) == B.EMD_ERR_ARG  # the warm start is the coarse solution
+    assert call(p, ok, nbytes=16) == B.EMD_ERR_WORKSPACE
+    assert call(p, ok, ws=ctypes.c_void_p(264)) == B.EMD_ERR_WORKSPACE
+    assert L.emd_restrict_time(None, 64, 4, 4, fake, None) == B.EMD_ERR_ARG
+    assert L.emd_restrict_time(fake, 64, 4, 0, fake, None) == B.EMD_ERR_ARG
+    assert L.emd_prolong_time(fake, 16, 4, 4, 64, 2, 0, 0, fake, None) == B.EMD_ERR_ARG
+    assert L.emd_prolong_time(fake, 0, 4, 4, 64, 0, 0, 0, fake, None) == B.EMD_ERR_ARG
+    assert L.emd_prolong_time(fake, 1 << 20, 4, 1 << 10, 64, 0, 0, 0, fake, None) == B.EMD_ERR_ARG
 
 
 def test_product_path_has_no_oracle_or_fallback():
