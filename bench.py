@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 NT, NR, DT, DX = 3000, 400, 1e-3, 12.5
 TOL = 1e-2
+MG_FACTOR = 10
 CELL_BYTES = 36  # algorithmic bytes per cell-update of the fused pass (first-try accept)
 METRIC = "PDHG cell-updates/s and EMD solves/s at fixed residual; HBM GB/s vs peak"
 WORKLOAD = (f"transmissive gather pair {NT}x{NR} (nt x nr), dt=1ms, dx=12.5m, 8 events, "
@@ -43,8 +44,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["transmissive", "marine"], default=None,
-                    help="run --warmup fixed-iteration solves of a named gather (for ncu) and exit")
+    ap.add_argument("--profile", choices=["transmissive", "marine", "transmissive-mg"], default=None,
+                    help="run --warmup solves of a named gather (for ncu) and exit")
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--workload", choices=["transmissive", "uneven48"], default="transmissive",
                     help="uneven48: 48 uneven gathers, batched solve vs one solve per gather")
@@ -94,8 +95,8 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1808_07284_gb300/csrc/emd_kernels.cuh", "paper_1808_07284_gb300/csrc/emd_pass_tma.cuh",
-                "paper_1808_07284_gb300/csrc/emd_api.cu"):  # the benchmark gather never takes the resident solve
+    # the device code of the fused pass (the benchmark gather never takes the resident solve)
+    for rel in ("paper_1808_07284_gb300/csrc/emd_kernels.cuh", "paper_1808_07284_gb300/csrc/emd_pass_tma.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -278,6 +279,33 @@ def run_gpu(a):
     achieved = CELL_BYTES * cells / t_pass / 1e9
     traffic = _traffic()
 
+    # ---- the same gather by the two-grid solve (Sec. 2.2, Sec. 3.3): time coarsened by 10 (the
+    #      paper's 3000 -> 301), coarse solve to the same residual, fine solve from its
+    #      interpolated solution to the same residual
+    mg = P.emd_default_mg_params(factor=MG_FACTOR, coarse_max_iter=200000, coarse_tol=TOL)
+    ws_mg = P.new_workspace(P.emd_mg_workspace_size(NT, NR, MG_FACTOR), dev)
+    for _ in range(3):
+        P.emd_dyn_solve_mg(o, p, DT, DX, params, mg, phi, m, ws_mg, stream)
+    mg_ms, mg_runs = [], []
+    for s in range(a.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fr, cr = P.emd_dyn_solve_mg(o, p, DT, DX, params, mg, phi, m, ws_mg, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mg_ms.append(e0.elapsed_time(e1))
+        mg_runs.append((fr, cr))
+    t_mg = max_over_ranks(sum(mg_ms) / len(mg_ms) / 1e3, dev)
+    fr, cr = mg_runs[-1]
+    multigrid = {
+        "solves_per_s": world / t_mg, "ms_per_solve": 1e3 * t_mg, "factor": MG_FACTOR,
+        "coarse_grid": [NR, -(-NT // MG_FACTOR)], "coarse_iters": cr.iters, "fine_iters": fr.iters,
+        "residual": fr.residual, "dist": fr.dist, "dist_single_solve": res.dist,
+        "speedup_vs_single_solve": t_step / t_mg, "launches_per_solve": fr.launches,
+        "note": "coarse and fine solves both run to the residual of the single solve; L2 flushed before each",
+    }
+
     # ---- end to end through the public API: pinned host gathers in, phi and the result out
     h_obs = torch.from_numpy(obs).pin_memory()
     h_pred = torch.from_numpy(pred).pin_memory()
@@ -304,6 +332,7 @@ def run_gpu(a):
                        "iters_per_solve": it_mean, "l2": "flushed (256 MB write) before every timed solve",
                        "reductions": "f64 above the warp", "parallelism": f"{world} independent solves"},
             "solves_per_s": world / t_step,
+            "multigrid": multigrid,
             "hbm_gbs_algorithmic": achieved,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -328,13 +357,15 @@ def run_gpu(a):
 def run_profile(a):
     """Fixed-iteration solves of one gather, nothing timed: the command ncu captures.
     transmissive: the benchmark gather (3000 x 400, 43 MB of state, L2-resident);
-    marine: one 8000 x 648 streamer gather (dt = 2 ms, dx = 25 m; 187 MB of state > L2)."""
+    marine: one 8000 x 648 streamer gather (dt = 2 ms, dx = 25 m; 187 MB of state > L2);
+    transmissive-mg: the benchmark gather by the two-grid solve, both stages to the benchmark
+    residual (--iters is ignored)."""
     import torch
 
     import paper_1808_07284_gb300 as P
     import synth
     dev = torch.device("cuda:0")
-    if a.profile == "transmissive":
+    if a.profile in ("transmissive", "transmissive-mg"):
         obs, pred = synth.gather_pair_transmissive(nt=NT, nr=NR, dt=DT, dx=DX)
         dt, dx = DT, DX
     else:
@@ -343,7 +374,11 @@ def run_profile(a):
     o = torch.from_numpy(obs).to(dev)
     p = torch.from_numpy(pred).to(dev)
     for _ in range(max(1, a.warmup)):
-        d, phi, m, info = P.emd(o, p, dt, dx, max_iter=a.iters)
+        if a.profile == "transmissive-mg":
+            d, phi, m, info = P.emd(o, p, dt, dx, max_iter=200000, tol=TOL, multigrid=dict(
+                factor=MG_FACTOR, coarse_max_iter=200000, coarse_tol=TOL))
+        else:
+            d, phi, m, info = P.emd(o, p, dt, dx, max_iter=a.iters)
     torch.cuda.synchronize()
     print(json.dumps({"profile": a.profile, "shape": list(obs.shape), "iters": info["iters"],
                       "dist": d, "status": info["status"]}))
