@@ -288,6 +288,19 @@ emd_status emd_dyn_solve_batched_mg(int B, const float *const *f_obs,
                                     emd_result *coarse, void *workspace, size_t ws_bytes,
                                     emd_stream_t stream);
 
+/*
+ * The conventional least-squares misfit the paper compares the EMD with (Sec. 2.1:
+ * f_L2 = 1/2 integral (Pcal - Pobs)^2 dx dt) and its adjoint source (Sec. 2.3:
+ * d f_L2 / d Pcal = Pcal - Pobs), discretised with the cell area A = dx*dt (dt when
+ * nr == 1): value (HOST, nullable) = A/2 * sum (Pcal - Pobs)^2, summed in FP64;
+ * grad_pred (device [nr][nt], nullable) = A (Pcal - Pobs); grad_obs (nullable) its
+ * negative.  Differences are taken in FP32.  Needs 256 bytes of workspace (any
+ * emd_workspace_size buffer will do).  Synchronises `stream` when value != NULL.
+ */
+emd_status emd_lsd(const float *f_obs, const float *f_pred, int nt, int nr, double dt, double dx,
+                   double *value, float *grad_pred, float *grad_obs, void *workspace,
+                   size_t ws_bytes, emd_stream_t stream);
+
 /* Static, human-readable name of a status code. */
 const char *emd_status_string(emd_status s);
 

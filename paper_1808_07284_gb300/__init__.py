@@ -19,7 +19,7 @@ from ._binding import (  # noqa: F401
     EmdError, EmdMgParams, EmdParams, EmdResult, emd_adjoint, emd_batched_mg_workspace_size,
     emd_batched_workspace_size, emd_decompose, emd_default_mg_params, emd_default_params,
     emd_dyn_solve, emd_dyn_solve_batched, emd_dyn_solve_batched_mg, emd_dyn_solve_mg,
-    emd_dyn_solve_noalloc, emd_mg_workspace_size, emd_prolong_time, emd_restrict_time,
+    emd_dyn_solve_noalloc, emd_lsd, emd_mg_workspace_size, emd_prolong_time, emd_restrict_time,
     emd_status_string, emd_tile_count, emd_workspace_size, lib, new_workspace,
 )
 
@@ -28,7 +28,8 @@ __all__ = [
     "emd_dyn_solve_batched", "emd_dyn_solve_noalloc", "emd_adjoint", "emd_default_params", "emd_workspace_size",
     "emd_batched_workspace_size", "emd_status_string", "emd_tile_count", "EmdError",
     "emd_dyn_solve_mg", "emd_dyn_solve_batched_mg", "emd_default_mg_params", "emd_mg_workspace_size",
-    "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time",
+    "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time", "emd_lsd", "lsd_loss",
+    "LSDFunction",
 ]
 
 
@@ -157,12 +158,41 @@ def _batched_autograd_function():
     return EMDBatchFunction
 
 
+def _lsd_autograd_function():
+    import torch
+
+    class LSDFunction(torch.autograd.Function):
+        """The least-squares misfit of Sec. 2.1 with its adjoint source (Sec. 2.3) from the
+        library's kernel: forward keeps the adjoint source it computed for backward."""
+
+        @staticmethod
+        def forward(ctx, f_pred, f_obs, dt, dx):
+            gp = torch.empty_like(f_pred, dtype=torch.float32)
+            v = emd_lsd(f_obs.detach().contiguous(), f_pred.detach().contiguous(), float(dt), float(dx),
+                        grad_pred=gp)
+            ctx.save_for_backward(gp)
+            return torch.tensor(v, dtype=torch.float32, device=f_pred.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (gp,) = ctx.saved_tensors
+            g = grad_out.to(torch.float32) * gp
+            return g, -g, None, None
+
+    return LSDFunction
+
+
 _EMDFunction = None
 _EMDBatchFunction = None
+_LSDFunction = None
 
 
 def __getattr__(name):
-    global _EMDFunction, _EMDBatchFunction
+    global _EMDFunction, _EMDBatchFunction, _LSDFunction
+    if name == "LSDFunction":
+        if _LSDFunction is None:
+            _LSDFunction = _lsd_autograd_function()
+        return _LSDFunction
     if name == "EMDFunction":
         if _EMDFunction is None:
             _EMDFunction = _autograd_function()
@@ -186,3 +216,9 @@ def emd_loss_batched(f_preds, f_obss, dts, dxs, **params):
     dts = [float(v) for v in (dts if hasattr(dts, "__len__") else [dts] * B)]
     dxs = [float(v) for v in (dxs if hasattr(dxs, "__len__") else [dxs] * B)]
     return __getattr__("EMDBatchFunction").apply(dts, dxs, params, *f_preds, *f_obss)
+
+
+def lsd_loss(f_pred, f_obs, dt, dx):
+    """Differentiable least-squares misfit (a 0-dim float32 tensor), the baseline the paper
+    compares the EMD with."""
+    return __getattr__("LSDFunction").apply(f_pred, f_obs, dt, dx)

@@ -22,7 +22,7 @@ EXPORTS = (
     "emd_dyn_solve", "emd_batched_workspace_size", "emd_dyn_solve_batched", "emd_adjoint",
     "emd_status_string", "emd_dyn_solve_noalloc", "emd_default_mg_params", "emd_mg_workspace_size",
     "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time", "emd_dyn_solve_mg",
-    "emd_dyn_solve_batched_mg",
+    "emd_dyn_solve_batched_mg", "emd_lsd",
 )
 
 
@@ -128,6 +128,9 @@ def lib() -> ctypes.CDLL:
                                                P(EmdResult), P(EmdResult), c_void_p, c_size_t,
                                                c_void_p]
         L.emd_dyn_solve_batched_mg.restype = c_int
+        L.emd_lsd.argtypes = [c_void_p, c_void_p, c_int, c_int, c_double, c_double, P(c_double),
+                              c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+        L.emd_lsd.restype = c_int
         L.emd_status_string.argtypes = [c_int]
         L.emd_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -356,3 +359,20 @@ def emd_dyn_solve_batched_mg(f_obs, f_pred, dts, dxs, params: EmdParams, mg: Emd
     if check and st != EMD_OK:
         raise EmdError(st, "emd_dyn_solve_batched_mg")
     return list(res), list(cres)
+
+
+def emd_lsd(f_obs, f_pred, dt, dx, grad_pred=None, grad_obs=None, workspace=None, stream=None) -> float:
+    """Least-squares misfit (Sec. 2.1) on the host; fills the adjoint sources if given."""
+    nr, nt = f_obs.shape
+    _check_grid(f_obs, nr, nt, "f_obs")
+    _check_grid(f_pred, nr, nt, "f_pred")
+    for t, name in ((grad_pred, "grad_pred"), (grad_obs, "grad_obs")):
+        if t is not None:
+            _check_grid(t, nr, nt, name)
+    ws = workspace if workspace is not None else new_workspace(256, f_obs.device)
+    v = c_double()
+    st = lib().emd_lsd(_ptr(f_obs), _ptr(f_pred), nt, nr, dt, dx, ctypes.byref(v), _ptr(grad_pred),
+                       _ptr(grad_obs), _ptr(ws), ws.numel(), _stream(stream))
+    if st != EMD_OK:
+        raise EmdError(st, "emd_lsd")
+    return v.value

@@ -17,6 +17,7 @@ LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libemd_gb300.so")
 SOURCES = [os.path.join(HERE, "csrc", "emd_api.cu"), os.path.join(HERE, "csrc", "emd_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "emd_kernels.cuh"),
+                  os.path.join(HERE, "csrc", "emd_lsd.cuh"),
                   os.path.join(HERE, "csrc", "emd_multigrid.cuh"),
                   os.path.join(HERE, "csrc", "emd_pass_tma.cuh"),
                   os.path.join(HERE, "csrc", "emd_resident.cuh"),

@@ -13,6 +13,7 @@
 
 #include "emd_gb300.h"
 #include "emd_kernels.cuh"
+#include "emd_lsd.cuh"
 #include "emd_multigrid.cuh"
 #include "emd_pass_tma.cuh"
 #include "emd_resident.cuh"
@@ -872,6 +873,30 @@ emd_status emd_dyn_solve_batched_mg(int B, const float *const *f_obs,
                                     emd_stream_t stream) {
   return mg_impl(B, f_obs, f_pred, nt, nr, dt, dx, params, mg, phi, m, results, coarse,
                  workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+emd_status emd_lsd(const float *f_obs, const float *f_pred, int nt, int nr, double dt, double dx,
+                   double *value, float *grad_pred, float *grad_obs, void *workspace,
+                   size_t ws_bytes, emd_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!f_obs || !f_pred || !size_ok(nt, nr)) return EMD_ERR_ARG;
+  if (!(dt > 0) || !std::isfinite(dt) || !(dx > 0) || !std::isfinite(dx)) return EMD_ERR_ARG;
+  if (!workspace || !aligned256(workspace) || ws_bytes < 256) return EMD_ERR_WORKSPACE;
+  double *acc = static_cast<double *>(workspace);
+  const size_t n = static_cast<size_t>(nt) * nr;
+  const double area = nr == 1 ? dt : dx * dt;
+  EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double), stream));
+  const int blocks = static_cast<int>(std::min<size_t>((n + kThreads - 1) / kThreads, 2048));
+  emd::k_lsd<<<blocks, kThreads, 0, stream>>>(f_obs, f_pred, n, static_cast<float>(area), grad_pred,
+                                              grad_obs, acc);
+  EMD_CK(cudaGetLastError());
+  if (value) {
+    double h = 0.0;
+    EMD_CK(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    EMD_CK(cudaStreamSynchronize(stream));
+    *value = 0.5 * area * h;
+  }
+  return EMD_OK;
 }
 
 const char *emd_status_string(emd_status s) {

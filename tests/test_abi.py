@@ -153,6 +153,16 @@ def test_two_grid_defaults_sizes_and_argument_errors(B):
     assert L.emd_prolong_time(fake, 1 << 20, 4, 1 << 10, 64, 0, 0, 0, fake, None) == B.EMD_ERR_ARG
 
 
+def test_lsd_argument_errors(B):
+    L = B.lib()
+    fake = ctypes.c_void_p(256)
+    v = ctypes.c_double()
+    assert L.emd_lsd(None, fake, 8, 4, 1e-3, 10.0, ctypes.byref(v), fake, None, fake, 256, None) == B.EMD_ERR_ARG
+    assert L.emd_lsd(fake, fake, 8, 4, -1.0, 10.0, ctypes.byref(v), fake, None, fake, 256, None) == B.EMD_ERR_ARG
+    assert L.emd_lsd(fake, fake, 8, 4, 1e-3, 10.0, ctypes.byref(v), fake, None, fake, 128, None) == B.EMD_ERR_WORKSPACE
+    assert L.emd_lsd(fake, fake, 8, 4, 1e-3, 10.0, ctypes.byref(v), fake, None, None, 256, None) == B.EMD_ERR_WORKSPACE
+
+
 def test_product_path_has_no_oracle_or_fallback():
     """The package and the CUDA sources never reach into the oracle or the input generators."""
     pkg = os.path.join(ROOT, "paper_1808_07284_gb300")

@@ -32,14 +32,28 @@ def _free_port():
         return s.getsockname()[1]
 
 
+def _shots():
+    """Five small shot pairs of uneven sizes (seeded)."""
+    import numpy as np
+    rng = np.random.default_rng(21)
+    shapes = [(2, 5), (4, 10), (3, 7), (3, 10), (5, 10)]
+    return [(np.maximum(rng.standard_normal(s), 0), np.maximum(rng.standard_normal(s), 0)) for s in shapes]
+
+
+def _solve(pair):
+    from oracle import emd_oracle as O
+    return O.pdhg(pair[0], pair[1], 0.1, 0.2, max_iter=60)["dist"]
+
+
 def _worker(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        sizes = [10, 40, 20, 30, 50]
-        mine = bench.shard_shots(sizes, world)[rank]
+        shots = _shots()
+        mine = bench.shard_shots([o.size for o, _ in shots], world)[rank]
+        dists = {s: _solve(shots[s]) for s in mine}  # this rank's share, solved independently
         t = bench.max_over_ranks(1.0 + rank)
-        out[rank] = (mine, t)
+        out[rank] = (mine, t, dists)
     finally:
         dist.destroy_process_group()
 
@@ -54,3 +68,8 @@ def test_two_gloo_ranks_share_shots_and_agree_on_the_max():
     assert sorted(shards[0] + shards[1]) == [0, 1, 2, 3, 4]
     assert not set(shards[0]) & set(shards[1])
     assert res[0][1] == res[1][1] == 2.0  # every rank sees the slowest rank's time
+    # the union of the ranks' results is the single-process result, shot by shot
+    merged = {**res[0][2], **res[1][2]}
+    assert sorted(merged) == [0, 1, 2, 3, 4]
+    for s, pair in enumerate(_shots()):
+        assert merged[s] == _solve(pair)
