@@ -131,7 +131,7 @@ Layout layout(int B, const int *nt, const int *nr) {
   L.states = 0;
   L.shots = align256(sizeof(State) * B);
   L.acc = L.shots + align256(sizeof(Shot) * B);
-  L.tiles = L.acc + align256(sizeof(double) * emd::kSpread * emd::kAcc * B);
+  L.tiles = L.acc + align256(sizeof(double) * emd::kAccBufs * emd::kSpread * emd::kAcc * B);
   L.misc = L.tiles + align256(sizeof(int) * static_cast<size_t>(L.max_tiles));
   L.header = L.misc + 256;
   size_t off = L.header;
@@ -413,7 +413,8 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
                          cudaMemcpyHostToDevice, stream));
   EMD_CK(cudaMemsetAsync(states, 0, sizeof(State) * B, stream));
   EMD_CK(cudaMemsetAsync(n_done, 0, 2 * sizeof(int), stream));
-  EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double) * emd::kSpread * emd::kAcc * B, stream));
+  EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double) * emd::kAccBufs * emd::kSpread * emd::kAcc * B,
+                         stream));
 
   Ctl ctl{};
   ctl.eps = p.eps;
@@ -468,7 +469,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
         cudaFuncSetAttribute(sh.solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(tsmem)) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sh.solve_tma, emd::kTmaThreads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sh.solve_tma, emd::kSolveThreads,
                                                       tsmem) == cudaSuccess &&
         per_sm >= 1) {
       int tiles = grid, passes = p.max_iter;
@@ -476,7 +477,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
       Ctl cctl = ctl;
       void *args[] = {&cctl, &tiles, &passes};
       EMD_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(sh.solve_tma), dim3(cgrid),
-                                         dim3(emd::kTmaThreads), args, tsmem, stream));
+                                         dim3(emd::kSolveThreads), args, tsmem, stream));
       persistent = true;
       n_launch += 1;
     }

@@ -72,13 +72,14 @@ struct alignas(16) State {
 };
 
 constexpr int kSpread = 16;         // copies of each accumulator (spreads the atomics)
+constexpr int kAccBufs = 2;         // accumulator sets per gather (the persistent solve alternates)
 // Solve-wide parameters, passed by value to every kernel.
 struct Ctl {
   double eps, xi, zeta, delta, tol, alpha0;
   int max_iter, check_every, ls_max_trials, linesearch, balance, debug_fault;
   const Shot *shots;
   State *states;
-  double *acc;                      // [gather][kSpread][kAcc] FP64 accumulators (zeroed)
+  double *acc;                      // [gather][kAccBufs][kSpread][kAcc] FP64 accumulators (zeroed)
   const int *tile_shot;             // global tile -> gather
   int *n_done;                      // gathers finished
   int *error;                       // set to 1 when a bounded device wait gives up
@@ -86,6 +87,11 @@ struct Ctl {
 };
 
 enum { ST_OK = 0, ST_NONFINITE = 3, ST_LINESEARCH = 4 };
+
+// Accumulator set `buf` of gather g: kSpread copies of kAcc values.
+__device__ __forceinline__ double *acc_of(const Ctl &c, int g, int buf = 0) {
+  return c.acc + (static_cast<size_t>(g) * kAccBufs + buf) * kSpread * kAcc;
+}
 
 // ------------------------------------------------------------------------------ helpers
 
@@ -142,9 +148,12 @@ __device__ __forceinline__ void block_accumulate(float (&v)[N], double *acc) {
   }
   compute_sync<NAMED>();
   if (threadIdx.x < N) {
-    double s = 0.0;
+    static_assert(kThreads / 32 == 8, "pairwise sum over eight warps");
+    double p[8];
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) s += static_cast<double>(part[w][threadIdx.x]);
+    for (int w = 0; w < 8; ++w) p[w] = static_cast<double>(part[w][threadIdx.x]);
+    // pairwise: three dependent FP64 adds instead of eight
+    const double s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
     atomicAdd(acc + threadIdx.x, s);
   }
 }
@@ -203,7 +212,9 @@ struct DecidePrep {
   int k;
 };
 
-__device__ __forceinline__ DecidePrep decide_prep(const Ctl &c, const State *st) {
+// St: State (global) or any copy of it with the same field names (shared memory).
+template <typename St>
+__device__ __forceinline__ DecidePrep decide_prep(const Ctl &c, const St *st) {
   const int lane = threadIdx.x & 31;
   DecidePrep d;
   d.k = st->k;
@@ -242,7 +253,9 @@ __device__ Decision decide_core(const Ctl &c, const DecidePrep &d, const double 
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const double Ppp = a_[0], Ppq = a_[1], Pqq = a_[2], Gpp = a_[3], Gpq = a_[4], Gqq = a_[5];
-  const bool finite = __all_sync(FULL, lane >= 9 || isfinite(a_[lane < 9 ? lane : 0]));
+  bool finite = true;  // constant indices keep a_ in registers
+#pragma unroll
+  for (int n = 0; n < 9; ++n) finite = finite && isfinite(a_[n]);
   Decision o;
   o.status = ST_OK;
   o.trials_now = 1;
@@ -393,7 +406,7 @@ __global__ void __launch_bounds__(kThreads) k_prepare(Ctl c) {
     if (lane == 0) red[warp][n] = v[n];
   }
   __syncthreads();
-  double *acc = c.acc + static_cast<size_t>(b) * kSpread * kAcc;
+  double *acc = acc_of(c, b);
   if (threadIdx.x < 5) {
     double t = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
@@ -548,7 +561,7 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
         v[3] += ex * ex + et * et;
       }
     }
-    double *acc = c.acc + static_cast<size_t>(s) * kSpread * kAcc;
+    double *acc = acc_of(c, s);
     block_accumulate<4>(v, acc + (lt % kSpread) * kAcc);
     if (!last_block(&st->ticket, S.ntiles)) return;
     double a_[4];
@@ -631,7 +644,7 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
       v[8] += dx_ * dx_ + dt_ * dt_;
     }
   }
-  double *acc = c.acc + static_cast<size_t>(s) * kSpread * kAcc;
+  double *acc = acc_of(c, s);
   block_accumulate<9>(v, acc + (lt % kSpread) * kAcc);
   if (!last_block(&st->ticket, S.ntiles)) return;
   DecidePrep pr;

@@ -108,12 +108,13 @@ __device__ __forceinline__ int ld_acquire_int(const int *p) {
   return v;
 }
 
-// Waits until *counter >= target or the gather has stopped (*done != 0).  False on timeout.
+// Waits until *counter >= target (modulo 2^32: cumulative counters of long solves may
+// wrap) or the gather has stopped (*done != 0).  False on timeout.
 __device__ __forceinline__ bool wait_counter(const unsigned *counter, unsigned target,
                                              const int *done) {
   const unsigned long long t0 = global_ns();
   for (unsigned n = 0;; ++n) {
-    if (ld_acquire(counter) >= target || ld_acquire_int(done)) return true;
+    if (static_cast<int>(ld_acquire(counter) - target) >= 0 || ld_acquire_int(done)) return true;
     if ((n & 255u) == 255u && global_ns() - t0 > kSpinLimitNs) return false;
     __nanosleep(64);
   }
@@ -165,25 +166,15 @@ struct TmaTile {
 
 constexpr int kTmaThreads = kThreads + 32;  // eight compute warps + one producer warp
 
-// Producer: stage tile t (of any gather) into `dst`, announcing its bytes on `full`.
-// A tile of a gather that has already stopped is marked inactive (the barrier phase
-// still completes, with no traffic).
-// kpass >= 0: the pass index of a persistent solve (the state's k may still lag it while
-// the previous decision is being taken); kpass < 0: use the state's k.
+// Geometry, buffers and stopping-test flag of tile t in pass k (no state read).
 template <int TI>
-__device__ __forceinline__ void stage_tile(const Ctl &c, int t, float *dst, uint64_t *full,
-                                           StageInfo &in, int kpass = -1) {
+__device__ __forceinline__ void tile_info(const Ctl &c, int t, int k, StageInfo &in) {
   using T = TmaTile<TI>;
   const int g = c.tile_shot[t];
   const Shot &S = c.shots[g];
-  const State *st = c.states + g;
-  const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(st));
-  const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(st) + 1);
   const int lt = t - S.tile0;
-  const int k = kpass >= 0 ? kpass : h0.x;
   in.gather = g;
   in.k = k;
-  in.active = !h0.y;
   in.i0 = (lt / S.tiles_j) * TI;
   in.j0 = (lt % S.tiles_j) * T::TJ;
   in.nr = S.nr;
@@ -191,20 +182,25 @@ __device__ __forceinline__ void stage_tile(const Ctl &c, int t, float *dst, uint
   in.ntp = S.ntp;
   in.rdx = S.rdx;
   in.rdt = S.rdt;
-  in.alpha = __int_as_float(h0.z);
-  in.coef = __int_as_float(h0.w);
-  in.theta = __int_as_float(h1.x);
-  in.inv = __int_as_float(h1.y);
-  in.fmean = __int_as_float(h1.z);
   in.interior = in.i0 >= 3 && in.i0 + TI + 2 < S.nr && in.j0 >= 5 && in.j0 + 124 < S.nt;
   in.need_res = (c.tol > 0.0 && (k + 1) % c.check_every == 0) || k + 1 >= c.max_iter;
   in.ph_cur = S.ph[k & 1];
   in.uxn = S.ux[(k + 1) % 3];
   in.utn = S.ut[(k + 1) % 3];
+}
+
+// Issues the six TMA box loads of tile `in` (pass in.k) into `dst`, announcing their
+// bytes on `full`; an inactive tile completes the barrier phase with no traffic.
+template <int TI>
+__device__ __forceinline__ void load_tile(const Ctl &c, const StageInfo &in, float *dst,
+                                          uint64_t *full) {
+  using T = TmaTile<TI>;
   if (!in.active) {
     mbar_arrive_tx(full, 0u);
     return;
   }
+  const Shot &S = c.shots[in.gather];
+  const int k = in.k;
   const int kp = k == 0 ? 0 : (k - 1) % 3, kc = k % 3;
   const int z[6] = {1 + 2 * kp, 2 + 2 * kp, 1 + 2 * kc, 2 + 2 * kc, 7 + ((k + 1) & 1), 0};
   fence_proxy_async_smem();  // the stage was last written by ordinary stores
@@ -215,12 +211,33 @@ __device__ __forceinline__ void stage_tile(const Ctl &c, int t, float *dst, uint
     tma_load_3d(dst + a * T::BOX, &S.tmap, in.j0 - 4, in.i0 - 2, z[a], full);
 }
 
+// Producer: stage tile t (of any gather) into `dst`, announcing its bytes on `full`,
+// with the step sizes and stop flag of the gather's state.  A tile of a gather that has
+// already stopped is marked inactive (the barrier phase still completes, with no
+// traffic).  kpass >= 0: the pass index of a persistent solve (the state's k may still
+// lag it while the previous decision is being taken); kpass < 0: use the state's k.
+template <int TI>
+__device__ __forceinline__ void stage_tile(const Ctl &c, int t, float *dst, uint64_t *full,
+                                           StageInfo &in, int kpass = -1) {
+  const State *st = c.states + c.tile_shot[t];
+  const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(st));
+  const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(st) + 1);
+  tile_info<TI>(c, t, kpass >= 0 ? kpass : h0.x, in);
+  in.active = !h0.y;
+  in.alpha = __int_as_float(h0.z);
+  in.coef = __int_as_float(h0.w);
+  in.theta = __int_as_float(h1.x);
+  in.inv = __int_as_float(h1.y);
+  in.fmean = __int_as_float(h1.z);
+  load_tile<TI>(c, in, dst, full);
+}
+
 // Compute warps: add the CTA's sums over `n` tiles of gather g to the gather's
 // accumulators; the CTA that completes the gather's tile count takes the decision.
 __device__ __forceinline__ void flush_gather(const Ctl &c, int g, int n, float (&v)[9]) {
   const Shot &S = c.shots[g];
   State *st = c.states + g;
-  double *acc = c.acc + static_cast<size_t>(g) * kSpread * kAcc;
+  double *acc = acc_of(c, g);
   block_accumulate<9, true>(v, acc + (blockIdx.x % kSpread) * kAcc);
   __shared__ bool last;
   __threadfence();
@@ -497,48 +514,128 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_pass_tma(Ctl c, int total
 // Persistent solve: every pass of the solve in one cooperative launch.
 //
 // Per gather, `tiles_done` counts finished tiles over all passes and `epoch` counts
-// decisions.  The CTA whose flush brings tiles_done to (k + 1) ntiles decides pass k
-// and then publishes epoch = k + 1.  The producer stages a tile of pass k once the
-// gather's pass k - 1 is complete (tiles_done >= k ntiles), which overlaps the first
-// tile's loads with the decision; the compute warps use the step sizes only after
-// epoch >= k.  At each pass boundary the compute warps tell the producer (mbarrier
-// `go`) whether any gather of this CTA is still running; the producer has staged the
-// pass's first tile before it knows, and the compute warps drain it when they stop.
+// decisions.  A decider warp (the tenth warp of the CTA that owns the gather's first tile)
+// waits for tiles_done to reach (k + 1) ntiles, takes decision k and publishes epoch =
+// k + 1; it loads the gather's state and prepares the FP64 decision inputs while pass k is
+// still being computed, so only the sums are left on the critical path.  The producer
+// stages a tile of pass k once the gather's pass k - 1 is complete (tiles_done >= k
+// ntiles), which overlaps the first tile's loads with the decision; the compute warps use
+// the step sizes only after epoch >= k.  At each pass boundary the compute warps tell the
+// producer (mbarrier `go`) whether any gather of this CTA is still running; the producer
+// has staged the pass's first tile before it knows, and the compute warps drain it when
+// they stop.
 
-// Compute warps: add the CTA's sums over `n` tiles of gather g (pass k) to the gather's
-// accumulators; the CTA that completes the pass takes the decision and publishes it.
+constexpr int kSolveThreads = kTmaThreads + 32;  // eight compute, one producer, one decider warp
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait until the cumulative counter reaches target (compared modulo 2^32, so long
+// solves may wrap it), then an acquire fence.  Spins without sleeping: the one warp that
+// calls it has nothing else to do, and a sleep would add its wake-up to the critical path.
+// False on timeout.
+__device__ __forceinline__ bool wait_count(const unsigned *counter, unsigned target) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned n = 0;; ++n) {
+    if (static_cast<int>(ld_relaxed(counter) - target) >= 0) break;
+    if ((n & 255u) == 255u && global_ns() - t0 > kSpinLimitNs) return false;
+  }
+  fence_acq_rel_gpu();
+  return true;
+}
+
+// Decider warp: decision k of gather g from its totals, written to the global state from
+// registers only (no read of what was just stored: a global load here is a round trip on
+// the critical path).  `trials` is the warp's running trial count of the gather.
+__device__ __forceinline__ void decide_publish(const Ctl &c, State *st, const DecidePrep &pr,
+                                               const double (&a_)[9], int g, int &trials) {
+  const Decision o = decide_core(c, pr, a_);
+  trials += o.trials_now;
+  if ((threadIdx.x & 31) != 0) return;
+  st->s_p2 = a_[0];
+  st->s_u1 = a_[6];
+  st->s_u2 = a_[7];
+  st->s_du2 = a_[8];
+  st->trials = trials;
+  if (o.status == ST_OK) {
+    st->alpha = o.alpha;
+    st->theta = o.theta;
+    st->coef = o.coef;
+    st->k = o.k_new;
+    st->alpha_f = static_cast<float>(o.alpha);
+    st->coef_f = static_cast<float>(o.coef);
+    st->theta_f = static_cast<float>(o.theta);
+    st->inv_f = 1.0f / (1.0f + static_cast<float>(c.eps * o.alpha));
+  } else {
+    st->status = o.status;
+  }
+  write_trace(c, g, pr.k, o, a_[0], pr.fnorm);
+  if (o.checked) {
+    st->r_feas = o.r_feas;
+    st->r_step = o.r_step;
+  }
+  if (o.done) {
+    st->done = 1;
+    atomicAdd(c.n_done, 1);
+  }
+}
+
+// The CTA that owns tile t when CTA b of `grid` owns [tile_lo(b), tile_lo(b + 1)): the
+// largest b with floor(b total / grid) <= t.
+__device__ __forceinline__ int tile_owner(int t, int total, int grid) {
+  return static_cast<int>((static_cast<long long>(t + 1) * grid - 1) / total);
+}
+
+// Compute warps: add the CTA's sums over `n` tiles of gather g to the gather's pass-k
+// accumulator set (FP64 reductions in L2), then the tile count with release semantics (it
+// also publishes this CTA's tile stores: the barrier gathers them under thread 0).
 __device__ __forceinline__ void flush_gather_persistent(const Ctl &c, int g, int n, int k,
                                                         float (&v)[9]) {
-  const Shot &S = c.shots[g];
-  State *st = c.states + g;
-  double *acc = c.acc + static_cast<size_t>(g) * kSpread * kAcc;
+  double *acc = acc_of(c, g, k & 1);
   block_accumulate<9, true>(v, acc + (blockIdx.x % kSpread) * kAcc);
-  __shared__ bool last;
-  __threadfence();
   compute_sync<true>();
-  if (threadIdx.x == 0) {
-    const unsigned full_count = static_cast<unsigned>(k + 1) * static_cast<unsigned>(S.ntiles);
-    last = atomicAdd(&st->tiles_done, static_cast<unsigned>(n)) + n == full_count;
-  }
-  compute_sync<true>();
-  if (last) {
-    __threadfence();
-    DecidePrep pr;
-    if (threadIdx.x < 32) pr = decide_prep(c, st);
-    double a_[9];
-    gather_totals<9, true>(acc, a_);
-    if (threadIdx.x < 32) decide(c, st, pr, a_, g);
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicExch(&st->epoch, static_cast<unsigned>(k + 1));
-    }
-  }
+  if (threadIdx.x == 0) red_release_add(&c.states[g].tiles_done, static_cast<unsigned>(n));
 #pragma unroll
   for (int q = 0; q < 9; ++q) v[q] = 0.0f;
 }
 
+// Decider warp: the totals of a gather's kSpread accumulator copies.  Lane n < 9 loads
+// the copies of value n and sums them pairwise in registers (four dependent FP64 adds, no
+// shuffles); one shuffle per value then gives every lane all nine.  Lanes past 8 repeat
+// value 0, so control flow stays uniform.
+__device__ __forceinline__ void warp_totals(const double *acc, double (&out)[9]) {
+  static_assert((kSpread & (kSpread - 1)) == 0, "pairwise sum over a power of two");
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int n = lane < 9 ? lane : 0;
+  double c[kSpread];
+#pragma unroll
+  for (int q = 0; q < kSpread; ++q) c[q] = __ldcg(acc + q * kAcc + n);
+#pragma unroll
+  for (int w = kSpread / 2; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) c[q] += c[q + w];
+#pragma unroll
+  for (int m = 0; m < 9; ++m) out[m] = __shfl_sync(FULL, c[0], m);
+}
+
 template <int TI, int MINB = 2>
-__global__ void __launch_bounds__(kTmaThreads, MINB)
+__global__ void __launch_bounds__(kSolveThreads, MINB)
     k_solve_tma(Ctl c, int total_tiles, int max_passes) {
   using T = TmaTile<TI>;
   extern __shared__ float4 dyn4[];
@@ -562,6 +659,42 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
     fence_mbar_init();
   }
   __syncthreads();
+
+  if (warp == kThreads / 32 + 1) {  // ---- decider warp: decisions of the gathers this CTA owns
+    constexpr unsigned FULL = 0xffffffffu;
+    const int g_lo = c.tile_shot[t_lo], g_hi = c.tile_shot[t_hi - 1];
+    for (int k = 0; k < max_passes; ++k) {
+      bool any = false;
+      for (int g = g_lo; g <= g_hi; ++g) {
+        const Shot &S = c.shots[g];
+        if (tile_owner(S.tile0, total_tiles, gridDim.x) != static_cast<int>(blockIdx.x)) continue;
+        State *st = c.states + g;
+        if (st->done) continue;  // this warp is the only writer of the gather's state
+        any = true;
+        const DecidePrep pr = decide_prep(c, st);  // overlaps pass k's compute
+        int trials = st->trials;
+        // every lane waits (see the compute warps' pass boundary)
+        const bool ok = __all_sync(
+            FULL, wait_count(&st->tiles_done, static_cast<unsigned>(k + 1) * static_cast<unsigned>(S.ntiles)));
+        if (!ok) {
+          if (lane == 0) atomicExch(c.error, 1);
+          return;
+        }
+        double a_[9];
+        double *acc = acc_of(c, g, k & 1);
+        warp_totals(acc, a_);
+        decide_publish(c, st, pr, a_, g, trials);
+        __syncwarp();  // the new state, before the release
+        if (lane == 0) st_release(&st->epoch, static_cast<unsigned>(k + 1));
+        // pass k + 2 adds into this set again; the release of epoch k + 2 (after decision
+        // k + 1) orders these zeros before any of its flushes
+#pragma unroll
+        for (int q = lane; q < kSpread * kAcc; q += 32) acc[q] = 0.0;
+      }
+      if (!any) return;
+    }
+    return;
+  }
 
   if (warp == kThreads / 32) {  // ---- producer warp: one lane stages every tile of every pass
     if (lane == 0) {
@@ -603,8 +736,10 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
   float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int i = 0;
   for (int k = 0; k < max_passes; ++k) {
-    // pass boundary: is any gather of this CTA still running after decision k - 1?
-    if (threadIdx.x == 0) {
+    // pass boundary: is any gather of this CTA still running after decision k - 1?  The
+    // whole of warp 0 waits (the same loads in every lane): a wait loop run by one lane
+    // leaves the warp split, and every later shuffle of it then costs ~10x.
+    if (warp == 0) {
       int go = 0;
       bool ok = true;
       int last_g = -1;
@@ -616,10 +751,14 @@ __global__ void __launch_bounds__(kTmaThreads, MINB)
         ok = wait_counter(&st->epoch, static_cast<unsigned>(k), &st->done);
         if (ok && !ld_acquire_int(&st->done)) go = 1;
       }
-      if (!ok) atomicExch(c.error, 1);
-      go_flag = ok ? go : 0;
-      hot_gather = -1;
-      mbar_arrive(&gob);
+      ok = __all_sync(0xffffffffu, ok);
+      go = __any_sync(0xffffffffu, go);
+      if (lane == 0) {
+        if (!ok) atomicExch(c.error, 1);
+        go_flag = ok ? go : 0;
+        hot_gather = -1;
+        mbar_arrive(&gob);
+      }
     }
     compute_sync<true>();
     if (!go_flag) {  // stop: drain the first tile the producer staged for this pass

@@ -170,12 +170,14 @@ def test_no_balancing(pkg):
     assert_parity(g, r)
 
 
+@pytest.mark.parametrize("nt,nr", [(200, 20), (600, 40)])
 @pytest.mark.parametrize("tol", [0.0, 1e-2])
-def test_launch_modes_agree(pkg, tol):
-    """One persistent launch (0), plain per-pass launches (1) and graph replays (2) run
-    the same iteration, with a fixed count and with a tolerance stop."""
-    obs, pred = synth.gather_pair_hyperbolic(nt=200, nr=20, seed=6)
-    dt, dx = (2e-3, 10.0) if tol == 0 else (1 / 199, 1 / 19)
+def test_launch_modes_agree(pkg, tol, nt, nr):
+    """Automatic (0: the shared-memory solve for 200 x 20, one persistent launch for
+    600 x 40), plain per-pass launches (1) and graph replays (2) run the same iteration,
+    with a fixed count and with a tolerance stop."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=nt, nr=nr, seed=6)
+    dt, dx = (2e-3, 10.0) if tol == 0 else (1 / (nt - 1), 1 / (nr - 1))
     runs = [gpu_solve(pkg, obs, pred, dt, dx, max_iter=130 if tol == 0 else 20000, tol=tol,
                       launch_mode=m) for m in (0, 1, 2)]
     for r in runs:
