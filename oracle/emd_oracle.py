@@ -28,6 +28,11 @@ listed with its reason in the design notes of the repository):
 * Q11 nr = 1 means a 1D problem: no x component, lambda = 4/dt^2, cell area dt.
 * Q12 the backtracking gives up after ``ls_max_trials`` trials (status LINESEARCH).
 * Q13 ``iters`` counts accepted outer iterations; trials are counted separately.
+* Q19 norm=2 selects the isotropic ground cost of the formulation the paper builds on,
+       ||u||_{1,2} = sum_ij sqrt((u^x_ij)^2 + (u^t_ij)^2), pairing the two flux components
+       of one grid index as the paper's ||u||_{1,1} sums them; the prox becomes the vector
+       shrink max(1 - alpha/||v||, 0) v and the conjugate in the gap (||w|| - 1)_+^2 / 2 eps.
+       norm=1 (default) is the paper's anisotropic ||u||_{1,1}.
 """
 
 from __future__ import annotations
@@ -39,6 +44,9 @@ import numpy as np
 
 BAL_NONE = 0
 BAL_MEAN = 1
+
+NORM_ANISO = 1  # ||u||_{1,1}: |u^x| + |u^t| per cell (Sec. 2.2)
+NORM_ISO = 2    # ||u||_{1,2}: sqrt((u^x)^2 + (u^t)^2) per cell (Q19)
 
 STATUS_OK = 0
 STATUS_NONFINITE = 3
@@ -61,6 +69,7 @@ class Params:
     linesearch: int = 1
     ls_norm: int = 2
     balance: int = BAL_MEAN
+    norm: int = NORM_ANISO
     phi_init: np.ndarray | None = field(default=None, repr=False)
     m_init: np.ndarray | None = field(default=None, repr=False)
 
@@ -156,10 +165,26 @@ def shrink(x, y):
     return out
 
 
-def primal_step(ux, ut, phi, alpha, eps, dt, dx):
-    """Eq. (primal-update): u^{k+1} = shrink(u^k + alpha grad phi^k, alpha) / (1 + eps alpha)."""
+def shrink_vec(vx, vt, y):
+    """Vector shrink of the isotropic norm (Q19): max(1 - y/||v||, 0) v per cell, v = (vx, vt);
+    the prox of y ||.||_2, as shrink is the prox of y |.|."""
+    vx = np.asarray(vx, np.float64)
+    vt = np.asarray(vt, np.float64)
+    n = np.sqrt(vx * vx + vt * vt)
+    scale = np.zeros_like(n)
+    big = n > y
+    scale[big] = 1.0 - y / n[big]
+    return scale * vx, scale * vt
+
+
+def primal_step(ux, ut, phi, alpha, eps, dt, dx, norm=NORM_ANISO):
+    """Eq. (primal-update): u^{k+1} = shrink(u^k + alpha grad phi^k, alpha) / (1 + eps alpha);
+    with norm=NORM_ISO the shrink acts on the vector (u^x, u^t) of each cell (Q19)."""
     gx, gt = gradient(phi, dt, dx)
     c = 1.0 / (1.0 + eps * alpha)
+    if norm == NORM_ISO:
+        nx, nt_ = shrink_vec(ux + alpha * gx, ut + alpha * gt, alpha)
+        return nx * c, nt_ * c
     return shrink(ux + alpha * gx, alpha) * c, shrink(ut + alpha * gt, alpha) * c
 
 
@@ -182,22 +207,31 @@ def _norm_scalar(d, ls_norm):
 
 # --------------------------------------------------------------------------- objective
 
-def objective(ux, ut, eps):
-    """Phi = ||u||_{1,1} + eps/2 ||u||_2^2 (Sec. 2.2) and its l1 part."""
-    l1 = float(np.abs(ux).sum() + np.abs(ut).sum())
+def objective(ux, ut, eps, norm=NORM_ANISO):
+    """Phi = ||u||_{1,1} + eps/2 ||u||_2^2 (Sec. 2.2) and its norm part (||u||_{1,2} with
+    norm=NORM_ISO, Q19)."""
+    if norm == NORM_ISO:
+        l1 = float(np.sqrt(ux * ux + ut * ut).sum())
+    else:
+        l1 = float(np.abs(ux).sum() + np.abs(ut).sum())
     l2 = float((ux * ux).sum() + (ut * ut).sum())
     return l1 + 0.5 * eps * l2, l1
 
 
-def duality_gap(ux, ut, phi, f, eps, dt, dx):
+def duality_gap(ux, ut, phi, f, eps, dt, dx, norm=NORM_ANISO):
     """dx dt [ Phi(u) - D(phi) ] with D(phi) = <phi, f> - sum h*(grad phi) (from the Lagrangian).
 
-    h(v) = |v| + eps/2 v^2 has the conjugate h*(w) = max(|w| - 1, 0)^2 / (2 eps).
+    h(v) = |v| + eps/2 v^2 has the conjugate h*(w) = max(|w| - 1, 0)^2 / (2 eps), per
+    component; for the isotropic norm h(v) = ||v|| + eps/2 ||v||^2 of the cell vector and
+    h*(w) = max(||w|| - 1, 0)^2 / (2 eps).
     """
     nr = phi.shape[0]
     gx, gt = gradient(phi, dt, dx)
-    prim, _ = objective(ux, ut, eps)
-    hs = (np.maximum(np.abs(gx) - 1.0, 0.0) ** 2 + np.maximum(np.abs(gt) - 1.0, 0.0) ** 2) / (2.0 * eps)
+    prim, _ = objective(ux, ut, eps, norm)
+    if norm == NORM_ISO:
+        hs = np.maximum(np.sqrt(gx * gx + gt * gt) - 1.0, 0.0) ** 2 / (2.0 * eps)
+    else:
+        hs = (np.maximum(np.abs(gx) - 1.0, 0.0) ** 2 + np.maximum(np.abs(gt) - 1.0, 0.0) ** 2) / (2.0 * eps)
     dual = float((phi * f).sum()) - float(hs.sum())
     return cell_area(nr, dt, dx) * (prim - dual)
 
@@ -261,7 +295,7 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
     r_feas = r_step = math.inf
     trace = []
     for k in range(p.max_iter):
-        nux, nut = primal_step(ux, ut, phi, alpha, p.eps, dt, dx)
+        nux, nut = primal_step(ux, ut, phi, alpha, p.eps, dt, dx, p.norm)
         if p.linesearch:
             a = alpha * math.sqrt(1.0 + theta)
             accepted = False
@@ -308,13 +342,13 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
         if p.tol > 0 and iters % p.check_every == 0 and max(r_feas, r_step) <= p.tol:
             break
 
-    phi_val, l1 = objective(ux, ut, p.eps)
+    phi_val, l1 = objective(ux, ut, p.eps, p.norm)
     out = dict(
         dist=area * phi_val, dist_l1=area * l1, phi=phi, ux=ux, ut=ut, f=f,
         iters=iters, trials=trials_total, status=status,
         residual=max(r_feas, r_step), r_feas=r_feas, r_step=r_step,
         alpha=alpha, theta=theta, imbalance=imbalance,
-        gap=duality_gap(ux, ut, phi, f, p.eps, dt, dx) if p.eps > 0 else float("nan"),
+        gap=duality_gap(ux, ut, phi, f, p.eps, dt, dx, p.norm) if p.eps > 0 else float("nan"),
     )
     if record:
         out["trace"] = np.array(trace)
