@@ -55,11 +55,21 @@ typedef enum {
   EMD_BAL_MEAN = 1  /* remove the mean of f first, so that the zero-flux problem is feasible */
 } emd_balance;
 
+/* Ground cost of the flux norm.  The paper's Phi uses ||u||_{1,1} = sum |u^x| + |u^t|
+ * (Sec. 2.2); the isotropic ||u||_{1,2} = sum sqrt((u^x)^2 + (u^t)^2), with u^x and u^t of
+ * one grid index paired, is the formulation of the work the paper builds on (its prox is
+ * the vector shrink max(1 - alpha/||v||, 0) v).  dist and dist_l1 use the chosen norm. */
+typedef enum {
+  EMD_NORM_ANISO = 1, /* ||u||_{1,1} (default, as printed)                                */
+  EMD_NORM_ISO = 2    /* ||u||_{1,2}                                                     */
+} emd_norm;
+
 /*
  * Solver parameters (Sec. 2.2 and Algorithm 1).  emd_default_params() fills the paper's
  * constants: eps = 1e-4, xi = 0.5, zeta = 0.99, delta = 1e5, plus max_iter = 2000,
  * tol = 0, check_every = 10, ls_max_trials = 40, linesearch = 1, ls_norm = 2,
- * balance = EMD_BAL_MEAN, no warm start, tile = 0, launch_mode = 0, no trace.
+ * balance = EMD_BAL_MEAN, no warm start, tile = 0, launch_mode = 0, no trace,
+ * norm = EMD_NORM_ANISO.
  */
 typedef struct {
   double eps;        /* regularisation epsilon of Phi = ||u||_{1,1} + eps/2 ||u||^2      */
@@ -96,6 +106,7 @@ typedef struct {
                         linesearch trials it took, and ||div u^{k+1} + f|| / ||f||.
                         Entries past a gather's last iteration are left untouched.
                         NULL = no history.                                                */
+  int norm;          /* emd_norm: EMD_NORM_ANISO (default) or EMD_NORM_ISO                */
 } emd_params;
 
 /* Host-side result of one solve.  Distances are in the units of dx*dt*|u|. */

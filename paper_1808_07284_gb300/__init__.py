@@ -14,7 +14,7 @@ library's kernels.
 from __future__ import annotations
 
 from ._binding import (  # noqa: F401
-    EMD_BAL_MEAN, EMD_BAL_NONE, EMD_ERR_ARG, EMD_ERR_CUDA, EMD_ERR_LINESEARCH,
+    EMD_BAL_MEAN, EMD_BAL_NONE, EMD_ERR_ARG, EMD_NORM_ANISO, EMD_NORM_ISO, EMD_ERR_CUDA, EMD_ERR_LINESEARCH,
     EMD_ERR_NONFINITE, EMD_ERR_TIMEOUT, EMD_ERR_WORKSPACE, EMD_OK, EXPORTS,
     EmdError, EmdMgParams, EmdParams, EmdResult, emd_adjoint, emd_batched_mg_workspace_size,
     emd_batched_workspace_size, emd_decompose, emd_default_mg_params, emd_default_params,
@@ -37,7 +37,8 @@ def emd(f_obs, f_pred, dt, dx, workspace=None, stream=None, check=True, multigri
     """One EMD solve.  Returns ``(dist, phi[nr, nt], m[2, nr, nt], info)``.
 
     ``params`` are ``emd_params`` fields (eps, xi, zeta, delta, alpha0, tol, max_iter,
-    check_every, ls_max_trials, linesearch, balance, phi_init, m_init, tile, launch_mode).
+    check_every, ls_max_trials, linesearch, balance, phi_init, m_init, tile, launch_mode,
+    norm: EMD_NORM_ANISO or EMD_NORM_ISO).
     ``multigrid``: None for one solve, or a dict of ``emd_mg_params`` fields (factor,
     coarse_max_iter, coarse_tol, interpolate_phi; ``{}`` = the Sec. 3.3 setting) for the
     two-grid solve of Sec. 2.2/3.3; ``info["coarse"]`` then describes the coarse solve.

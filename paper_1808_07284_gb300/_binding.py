@@ -16,6 +16,7 @@ c_double, c_int, c_size_t, c_void_p = ctypes.c_double, ctypes.c_int, ctypes.c_si
 
 EMD_OK, EMD_ERR_ARG, EMD_ERR_CUDA, EMD_ERR_NONFINITE, EMD_ERR_LINESEARCH, EMD_ERR_TIMEOUT, EMD_ERR_WORKSPACE = range(7)
 EMD_BAL_NONE, EMD_BAL_MEAN = 0, 1
+EMD_NORM_ANISO, EMD_NORM_ISO = 1, 2
 
 EXPORTS = (
     "emd_default_params", "emd_tile_count", "emd_workspace_size", "emd_decompose",
@@ -36,7 +37,7 @@ class EmdParams(ctypes.Structure):
         ("linesearch", c_int), ("ls_norm", c_int), ("balance", c_int),
         ("phi_init", c_void_p), ("m_init", c_void_p),
         ("tile", c_int), ("launch_mode", c_int), ("debug_fault", c_int),
-        ("trace", c_void_p),
+        ("trace", c_void_p), ("norm", c_int),
     ]
 
 

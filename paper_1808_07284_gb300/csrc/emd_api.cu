@@ -157,6 +157,7 @@ bool params_ok(const emd_params &p) {
   if (p.balance != EMD_BAL_NONE && p.balance != EMD_BAL_MEAN) return false;
   if (p.tile < 0 || p.tile > kNumShapes) return false;
   if (p.launch_mode < 0 || p.launch_mode > 2) return false;
+  if (p.norm != EMD_NORM_ANISO && p.norm != EMD_NORM_ISO) return false;
   return true;
 }
 
@@ -429,6 +430,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   ctl.linesearch = p.linesearch;
   ctl.balance = p.balance;
   ctl.debug_fault = p.debug_fault;
+  ctl.iso = p.norm == EMD_NORM_ISO;
   ctl.shots = dshots;
   ctl.states = states;
   ctl.acc = acc;
@@ -728,6 +730,7 @@ void emd_default_params(emd_params *p) {
   p->launch_mode = 0;
   p->debug_fault = 0;
   p->trace = nullptr;
+  p->norm = EMD_NORM_ANISO;
 }
 
 int emd_tile_count(void) { return kNumShapes; }

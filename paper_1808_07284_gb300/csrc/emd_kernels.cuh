@@ -77,6 +77,7 @@ constexpr int kAccBufs = 2;         // accumulator sets per gather (the persiste
 struct Ctl {
   double eps, xi, zeta, delta, tol, alpha0;
   int max_iter, check_every, ls_max_trials, linesearch, balance, debug_fault;
+  int iso;                          // 1: isotropic ground cost ||u||_{1,2}; 0: ||u||_{1,1}
   const Shot *shots;
   State *states;
   double *acc;                      // [gather][kAccBufs][kSpread][kAcc] FP64 accumulators (zeroed)
@@ -122,6 +123,36 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 __device__ __forceinline__ float shrinkf(float v, float a) {
   const float av = fabsf(v);
   return av >= a ? copysignf(av - a, v) : 0.0f;
+}
+
+// The primal prox of one cell, v = u^k + alpha grad phi^k: shrink per component for the
+// paper's ||u||_{1,1} (Sec. 2.2), or the vector shrink max(1 - alpha/||v||, 0) v for the
+// isotropic ||u||_{1,2}; both then divided by 1 + eps alpha (inv).
+__device__ __forceinline__ void prox_cell(float vx, float vt, float alpha, float inv, bool iso,
+                                          float &nx, float &nt) {
+  if (iso) {
+    const float n = sqrtf(vx * vx + vt * vt);
+    const float s = n > alpha ? (1.0f - alpha / n) * inv : 0.0f;
+    nx = s * vx;
+    nt = s * vt;
+  } else {
+    nx = shrinkf(vx, alpha) * inv;
+    nt = shrinkf(vt, alpha) * inv;
+  }
+}
+
+// The norm of one cell's flux and the conjugate term (|w| - 1)_+^2 of the dual, per the
+// ground cost (the duality gap's h* of Sec. 2.2's Lagrangian).
+__device__ __forceinline__ float cell_norm(float ux, float ut, bool iso) {
+  return iso ? sqrtf(ux * ux + ut * ut) : fabsf(ux) + fabsf(ut);
+}
+__device__ __forceinline__ float cell_conj(float gx, float gt, bool iso) {
+  if (iso) {
+    const float e = fmaxf(sqrtf(gx * gx + gt * gt) - 1.0f, 0.0f);
+    return e * e;
+  }
+  const float ex = fmaxf(fabsf(gx) - 1.0f, 0.0f), et = fmaxf(fabsf(gt) - 1.0f, 0.0f);
+  return ex * ex + et * et;
 }
 
 // Barrier over the kThreads compute threads: the whole CTA, or (NAMED) the compute
@@ -554,11 +585,10 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
         const size_t g = static_cast<size_t>(gi) * nt + gj;
         S.m_out[g] = ux;
         S.m_out[static_cast<size_t>(nr) * nt + g] = ut;
-        v[0] += fabsf(ux) + fabsf(ut);
+        v[0] += cell_norm(ux, ut, c.iso);
         v[1] += ux * ux + ut * ut;
         v[2] += PH[o] * (FF[o] - fmean);
-        const float ex = fmaxf(fabsf(gx) - 1.0f, 0.0f), et = fmaxf(fabsf(gt) - 1.0f, 0.0f);
-        v[3] += ex * ex + et * et;
+        v[3] += cell_conj(gx, gt, c.iso);
       }
     }
     double *acc = acc_of(c, s);
@@ -582,8 +612,7 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
       if (col_in && gi >= 0 && gi < nr) {
         const float gx = gi > 0 ? (PH[o] - PH[o - W]) * rdx : 0.0f;
         const float gt = gj > 0 ? (PH[o] - PH[o - 1]) * rdt : 0.0f;
-        nx = shrinkf(UBx[o] + alpha * gx, alpha) * inv;
-        nt_ = shrinkf(UBt[o] + alpha * gt, alpha) * inv;
+        prox_cell(UBx[o] + alpha * gx, UBt[o] + alpha * gt, alpha, inv, c.iso, nx, nt_);
         if (r >= 2 && r < TI + 2 && c_ >= 4 && c_ < TJ + 4) {
           S.ux[kn][gi * ntp + gj] = nx;
           S.ut[kn][gi * ntp + gj] = nt_;
@@ -639,7 +668,7 @@ __global__ void __launch_bounds__(kThreads) k_pass(Ctl c) {
       v[5] += gqx * gqx + gqt * gqt;
       const float nx = UAx[o], nt_ = UAt[o];
       const float dx_ = nx - UBx[o], dt_ = nt_ - UBt[o];
-      v[6] += fabsf(nx) + fabsf(nt_);
+      v[6] += cell_norm(nx, nt_, c.iso);
       v[7] += nx * nx + nt_ * nt_;
       v[8] += dx_ * dx_ + dt_ * dt_;
     }

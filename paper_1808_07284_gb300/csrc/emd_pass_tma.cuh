@@ -151,6 +151,7 @@ struct StageInfo {
   int gather, k, active, i0, j0, nr, nt, ntp;
   int interior;  // every staged cell is inside the grid, away from its first/last row/column
   int need_res;  // this pass's residual sums are read (a stopping test or the last iteration)
+  int iso;       // isotropic ground cost (vector shrink in the prox)
   float alpha, coef, theta, inv, fmean, rdx, rdt;
   float *ph_cur, *uxn, *utn;
 };
@@ -184,6 +185,7 @@ __device__ __forceinline__ void tile_info(const Ctl &c, int t, int k, StageInfo 
   in.rdt = S.rdt;
   in.interior = in.i0 >= 3 && in.i0 + TI + 2 < S.nr && in.j0 >= 5 && in.j0 + 124 < S.nt;
   in.need_res = (c.tol > 0.0 && (k + 1) % c.check_every == 0) || k + 1 >= c.max_iter;
+  in.iso = c.iso;
   in.ph_cur = S.ph[k & 1];
   in.uxn = S.ux[(k + 1) % 3];
   in.utn = S.ut[(k + 1) % 3];
@@ -263,8 +265,10 @@ __device__ __forceinline__ void flush_gather(const Ctl &c, int g, int n, float (
 // phi^k, then q), FF (f, then p); smem row r <-> receiver i0 - 2 + r, column c <->
 // time sample j0 - 4 + c.  Adds the tile's sums to v.  All compute threads.
 // INTERIOR: the tile is away from every edge of the grid, so no cell needs a boundary
-// mask (the masked instantiation gives the same values there).
-template <int TI, bool INTERIOR>
+// mask (the masked instantiation gives the same values there).  ISO: the isotropic
+// ground cost (vector shrink); a template parameter because a per-cell branch on it cost
+// 5 % of the pass.
+template <int TI, bool INTERIOR, bool ISO>
 __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int lane, int warp,
                                           float (&v)[9]) {
   using T = TmaTile<TI>;
@@ -346,8 +350,10 @@ __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int l
       const float gx = xl ? (ph[q] - phu[q]) * rdx : 0.0f;
       const float gt = ctl[q] ? (ph[q] - (q == 0 ? phL : ph[q - 1])) * rdt : 0.0f;
       const bool in_ = rin && cin[q];
-      nx[q] = in_ ? shrinkf(bx[q] + alpha * gx, alpha) * inv : 0.0f;
-      nv[q] = in_ ? shrinkf(bt[q] + alpha * gt, alpha) * inv : 0.0f;
+      float ax_, at_;
+      prox_cell(bx[q] + alpha * gx, bt[q] + alpha * gt, alpha, inv, ISO, ax_, at_);
+      nx[q] = in_ ? ax_ : 0.0f;
+      nv[q] = in_ ? at_ : 0.0f;
     }
     st4(UAx + o, nx);
     st4(UAt + o, nv);
@@ -493,10 +499,17 @@ __global__ void __launch_bounds__(kTmaThreads, MINB) k_pass_tma(Ctl c, int total
     }
     const StageInfo in = info[s];
     if (in.active) {
-      if (in.interior)
-        pass_tile<TI, true>(in, sbase + s * T::STAGE, lane, warp, v);
-      else
-        pass_tile<TI, false>(in, sbase + s * T::STAGE, lane, warp, v);
+      if (in.iso) {
+        if (in.interior)
+          pass_tile<TI, true, true>(in, sbase + s * T::STAGE, lane, warp, v);
+        else
+          pass_tile<TI, false, true>(in, sbase + s * T::STAGE, lane, warp, v);
+      } else {
+        if (in.interior)
+          pass_tile<TI, true, false>(in, sbase + s * T::STAGE, lane, warp, v);
+        else
+          pass_tile<TI, false, false>(in, sbase + s * T::STAGE, lane, warp, v);
+      }
       ++seg;
       const int tn = t + 1;
       const int gn = tn < t_hi ? c.tile_shot[tn] : -1;
@@ -802,10 +815,17 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
         in.theta = hot[2];
         in.inv = hot[3];
         in.fmean = hot[4];
-        if (in.interior)
-          pass_tile<TI, true>(in, sbase + s * T::STAGE, lane, warp, v);
-        else
-          pass_tile<TI, false>(in, sbase + s * T::STAGE, lane, warp, v);
+        if (in.iso) {
+          if (in.interior)
+            pass_tile<TI, true, true>(in, sbase + s * T::STAGE, lane, warp, v);
+          else
+            pass_tile<TI, false, true>(in, sbase + s * T::STAGE, lane, warp, v);
+        } else {
+          if (in.interior)
+            pass_tile<TI, true, false>(in, sbase + s * T::STAGE, lane, warp, v);
+          else
+            pass_tile<TI, false, false>(in, sbase + s * T::STAGE, lane, warp, v);
+        }
         ++seg;
         const int tn = t + 1;
         const int gn = tn < t_hi ? c.tile_shot[tn] : -1;

@@ -116,8 +116,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_solve_resident(Ctl c) {
         const float ph = PH[q];
         const float gx = i > 0 ? (ph - PH[q - nt]) * rdx : 0.0f;
         const float gt = j > 0 ? (ph - PH[q - 1]) * rdt : 0.0f;
-        Nx[q] = shrinkf(Bx[q] + alpha * gx, alpha) * inv;
-        Nv[q] = shrinkf(Bt[q] + alpha * gt, alpha) * inv;
+        prox_cell(Bx[q] + alpha * gx, Bt[q] + alpha * gt, alpha, inv, c.iso, Nx[q], Nv[q]);
       }
     }
     __syncthreads();

@@ -72,7 +72,7 @@ def assert_parity(g, r, trials=True, exact_trials=False):
     assert rel_l2(u_g, u_r) <= PHI_RTOL
 
 
-def parity_until_first_flip(P, obs, pred, dt, dx, K, **kw):
+def parity_until_first_flip(P, obs, pred, dt, dx, K, gpu_kw=None, **kw):
     """Element parity up to the first linesearch decision the GPU takes differently.
 
     When the two sides of Algorithm 1's test nearly tie, FP32 iterates (whose sums drift
@@ -82,9 +82,11 @@ def parity_until_first_flip(P, obs, pred, dt, dx, K, **kw):
     iteration that differs the decisions must agree exactly and alpha, theta to 1e-9; at
     that iteration the oracle's two sides must have been within 1e-2 of each other (a near
     tie); and the iterates are compared element-wise just before it.  Returns that
-    iteration count (K when every decision agrees)."""
+    iteration count (K when every decision agrees).  gpu_kw: launch options of the GPU
+    side only (tile, launch_mode)."""
+    gk = dict(gpu_kw or {})
     r = O.pdhg(obs, pred, dt, dx, max_iter=K, record=True, **kw)
-    g = gpu_solve(P, obs, pred, dt, dx, max_iter=K, trace=True, **kw)
+    g = gpu_solve(P, obs, pred, dt, dx, max_iter=K, trace=True, **kw, **gk)
     n = min(g["info"]["iters"], r["iters"])
     gt, ot = g["trace"][:n], r["trace"][:n]
     diff = np.where(gt[:, 2].astype(int) != ot[:, 2].astype(int))[0]
@@ -98,7 +100,7 @@ def parity_until_first_flip(P, obs, pred, dt, dx, K, **kw):
     assert ot[m, 5] < 1e-2, f"iteration {m}: the GPU decided differently away from a near tie"
     assert m >= 1
     r_m = O.pdhg(obs, pred, dt, dx, max_iter=m, **kw)
-    assert_parity(gpu_solve(P, obs, pred, dt, dx, max_iter=m, **kw), r_m, exact_trials=True)
+    assert_parity(gpu_solve(P, obs, pred, dt, dx, max_iter=m, **kw, **gk), r_m, exact_trials=True)
     return m
 
 
@@ -447,3 +449,44 @@ def test_1d_shift_sweep_61_shifts_batched(pkg):
         assert np.all(np.diff(vals) >= -2e-3 * vals.max())  # non-decreasing in |shift|
     far = np.abs(shifts) >= 0.2
     assert np.ptp(l1[far]) <= 2e-3 * l1.max()  # plateau once the signals no longer overlap
+
+
+# ----------------------------------------------------------------------------- isotropic ground cost
+
+@pytest.mark.parametrize("nt,nr,kw", [
+    (256, 64, dict()),                 # persistent TMA solve
+    (64, 64, dict()),                  # shared-memory resident solve (4096 cells)
+    (256, 64, dict(tile=1)),           # plain per-pass kernel, 16 x 120 tiles
+    (200, 40, dict(launch_mode=1)),    # per-pass TMA launches
+])
+def test_isotropic_parity(pkg, nt, nr, kw):
+    """norm = EMD_NORM_ISO (reading Q19) on every solver path against the oracle's
+    isotropic Algorithm 1, element by element up to the first near-tie decision."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=nt, nr=nr, seed=11)
+    parity_until_first_flip(pkg, obs, pred, 2e-3, 10.0, 600, gpu_kw=kw, norm=O.NORM_ISO)
+
+
+def test_isotropic_batched_equals_single(pkg):
+    gathers = [synth.gather_pair_hyperbolic(nt=nt, nr=nr, seed=s) for nt, nr, s in [(300, 50, 1), (180, 30, 2)]]
+    dev = torch.device("cuda:0")
+    O_ = [torch.from_numpy(a).to(dev) for a, _ in gathers]
+    P_ = [torch.from_numpy(b).to(dev) for _, b in gathers]
+    d, phis, _, infos = pkg.emd_batched(O_, P_, 2e-3, 10.0, max_iter=300, norm=pkg.EMD_NORM_ISO)
+    for b in range(2):
+        d1, phi1, _, i1 = pkg.emd(O_[b], P_[b], 2e-3, 10.0, max_iter=300, norm=pkg.EMD_NORM_ISO)
+        assert infos[b]["iters"] == i1["iters"] == 300
+        assert d[b] == pytest.approx(d1, rel=2e-3)
+        assert rel_l2(phis[b].double().cpu().numpy(), phi1.double().cpu().numpy()) <= 2e-2
+
+
+def test_isotropic_converged_against_oracle_and_bracket(pkg):
+    """Normalised domain, run to residual 1e-3: the isotropic distance matches the oracle's
+    converged one and lies between the anisotropic distance over sqrt(2) and it."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=96, nr=12, seed=3)
+    dt, dx = 1 / 95, 1 / 11
+    gi = gpu_solve(pkg, obs, pred, dt, dx, max_iter=40000, tol=1e-3, norm=O.NORM_ISO)
+    ga = gpu_solve(pkg, obs, pred, dt, dx, max_iter=40000, tol=1e-3)
+    ri = O.pdhg(obs, pred, dt, dx, max_iter=40000, tol=1e-3, norm=O.NORM_ISO)
+    assert gi["info"]["residual"] <= 1e-3 and ri["residual"] <= 1e-3
+    assert gi["info"]["dist_l1"] == pytest.approx(ri["dist_l1"], rel=2e-2)
+    assert ga["info"]["dist_l1"] / np.sqrt(2) <= gi["info"]["dist_l1"] <= ga["info"]["dist_l1"]
