@@ -44,29 +44,39 @@ struct Shape {
   void (*iter_tma)(Ctl, int);
   void (*solve_tma)(Ctl, int, int);  // every pass in one cooperative launch
   int minb;                           // TMA pass: CTAs per SM it is compiled for
+  int nw, ns;                         // persistent solve: compute warps, shared-memory stages
 };
 
 #define EMD_SHAPE(TI, W) \
-  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr, nullptr, 0 }
-#define EMD_TMA_SHAPE(TI, MINB)                                                             \
+  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr, nullptr, 0, 0, 0 }
+#define EMD_TMA_SHAPE(TI, MINB, NW, NS)                                                     \
   Shape {                                                                                   \
     TI, 128, nullptr, emd::k_pass<TI, 128, true>, emd::k_pass_tma<TI, MINB>,                \
-        emd::k_solve_tma<TI, MINB>, MINB                                                    \
+        emd::k_solve_tma<TI, MINB, NW, NS>, MINB, NW, NS                                    \
   }
-const Shape kShapes[] = {EMD_SHAPE(16, 128),    EMD_SHAPE(8, 128),     EMD_SHAPE(32, 128),
-                         EMD_SHAPE(8, 256),     EMD_SHAPE(16, 256),    EMD_SHAPE(1, 256),
-                         EMD_TMA_SHAPE(13, 2),  EMD_TMA_SHAPE(8, 3),   EMD_TMA_SHAPE(21, 1)};
+// (A 13 x 120 shape with one CTA per SM, sixteen compute warps and four stages -- three
+// tiles in flight -- passed the parity tests but was 20-45 % slower on gathers larger
+// than L2 than two CTAs of eight warps with two stages each; it is not compiled.)
+const Shape kShapes[] = {EMD_SHAPE(16, 128),          EMD_SHAPE(8, 128),
+                         EMD_SHAPE(32, 128),          EMD_SHAPE(8, 256),
+                         EMD_SHAPE(16, 256),          EMD_SHAPE(1, 256),
+                         EMD_TMA_SHAPE(13, 2, 8, 2),  EMD_TMA_SHAPE(8, 3, 8, 2),
+                         EMD_TMA_SHAPE(21, 1, 8, 2)};
 #undef EMD_SHAPE
 #undef EMD_TMA_SHAPE
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kTmaShape = 6;         // 13 x 120, two CTAs per SM: the untuned default
 constexpr int kTmaFirst = 6, kTmaLast = 8;
 
-// Dynamic shared memory of the plain pass / finalize pass of a shape, and of its
-// iteration pass (two TMA stages of six (TI + 4) x 128 planes, plus alignment slack).
+// Dynamic shared memory of the plain pass / finalize pass of a shape, of its per-pass
+// TMA kernel (two stages of six (TI + 4) x 128 planes, plus alignment slack) and of its
+// persistent solve (ns such stages).
 size_t smem_bytes(const Shape &s) { return sizeof(float) * 6u * (s.ti + 4) * s.w; }
 size_t iter_smem_bytes(const Shape &s) {
   return s.iter_tma ? 2u * 6u * (s.ti + 4) * 128u * sizeof(float) + 128u : smem_bytes(s);
+}
+size_t solve_smem_bytes(const Shape &s) {
+  return static_cast<size_t>(s.ns) * 6u * (s.ti + 4) * 128u * sizeof(float) + 128u;
 }
 
 // cuTensorMapEncodeTiled, reached through the runtime (no link against libcuda).
@@ -268,9 +278,9 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
 
 // Tile-shape autotuner of the TMA pass.  The first default-tile solve of a (device,
 // gather sizes) configuration times each TMA shape on the caller's own data -- two short
-// fixed-iteration solves per shape, plain launches, whose difference is the per-pass
-// cost -- and keeps the fastest for the rest of the process.  The trial solves stop
-// before the finalize pass, so they write the workspace only.
+// fixed-iteration persistent solves per shape, whose difference is the per-pass cost --
+// and keeps the fastest for the rest of the process.  The trial solves stop before the
+// finalize pass, so they write the workspace only.
 std::mutex g_tune_lock;
 std::map<std::vector<long long>, int> g_tuned;
 
@@ -299,7 +309,7 @@ int autotune_shape(int B, const float *const *f_obs, const float *const *f_pred,
     q.tile = shape + 1;
     q.max_iter = iters;
     q.tol = 0.0;
-    q.launch_mode = 1;
+    q.launch_mode = 0;  // the persistent solve, which default solves run
     q.trace = nullptr;
     if (cudaEventRecord(e0, stream) != cudaSuccess) return -1.0f;
     SolveExtra trial = x;
@@ -466,20 +476,21 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   bool persistent = false;
   if (!resident && p.launch_mode == 0 && sh.solve_tma) {
     int dev = 0, coop = 0, per_sm = 0;
-    const size_t tsmem = iter_smem_bytes(sh);
+    const size_t tsmem = solve_smem_bytes(sh);
+    const int tthreads = (sh.nw + 2) * 32;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
         cudaFuncSetAttribute(sh.solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(tsmem)) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sh.solve_tma, emd::kSolveThreads,
-                                                      tsmem) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sh.solve_tma, tthreads, tsmem) ==
+            cudaSuccess &&
         per_sm >= 1) {
       int tiles = grid, passes = p.max_iter;
       const int cgrid = std::min(tiles, std::min(per_sm, sh.minb) * sm_count());
       Ctl cctl = ctl;
       void *args[] = {&cctl, &tiles, &passes};
       EMD_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(sh.solve_tma), dim3(cgrid),
-                                         dim3(emd::kSolveThreads), args, tsmem, stream));
+                                         dim3(tthreads), args, tsmem, stream));
       persistent = true;
       n_launch += 1;
     }

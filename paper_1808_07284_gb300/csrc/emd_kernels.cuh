@@ -155,37 +155,40 @@ __device__ __forceinline__ float cell_conj(float gx, float gt, bool iso) {
   return ex * ex + et * et;
 }
 
-// Barrier over the kThreads compute threads: the whole CTA, or (NAMED) the compute
-// warps only, when a CTA also holds a producer warp that does not take part.
-template <bool NAMED>
+// Barrier over the NW * 32 compute threads: the whole CTA, or (NAMED) the compute warps
+// only, when a CTA also holds producer / decider warps that do not take part.
+template <bool NAMED, int NW = kThreads / 32>
 __device__ __forceinline__ void compute_sync() {
   if (NAMED)
-    asm volatile("bar.sync 1, %0;\n" ::"n"(kThreads) : "memory");
+    asm volatile("bar.sync 1, %0;\n" ::"n"(NW * 32) : "memory");
   else
     __syncthreads();
 }
 
-// Reduce N per-thread FP32 partials of a CTA: FP32 within the warp, FP64 across warps,
-// then one FP64 atomic add per value into acc[0..N).  Every compute thread must call it.
-template <int N, bool NAMED = false>
+// Reduce N per-thread FP32 partials of a CTA's NW compute warps: FP32 within the warp,
+// FP64 across warps (pairwise: log2 NW dependent adds), then one FP64 atomic add per value
+// into acc[0..N).  Every compute thread must call it.
+template <int N, bool NAMED = false, int NW = kThreads / 32>
 __device__ __forceinline__ void block_accumulate(float (&v)[N], double *acc) {
+  static_assert((NW & (NW - 1)) == 0 && N <= NW * 32, "pairwise sum over a power of two");
   // acc points at this CTA's copy: acc[0..N)
-  __shared__ float part[kThreads / 32][N];
+  __shared__ float part[NW][N];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int n = 0; n < N; ++n) {
     const float w = warp_sum(v[n]);
     if (lane == 0) part[warp][n] = w;
   }
-  compute_sync<NAMED>();
+  compute_sync<NAMED, NW>();
   if (threadIdx.x < N) {
-    static_assert(kThreads / 32 == 8, "pairwise sum over eight warps");
-    double p[8];
+    double p[NW];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) p[w] = static_cast<double>(part[w][threadIdx.x]);
-    // pairwise: three dependent FP64 adds instead of eight
-    const double s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
-    atomicAdd(acc + threadIdx.x, s);
+    for (int w = 0; w < NW; ++w) p[w] = static_cast<double>(part[w][threadIdx.x]);
+#pragma unroll
+    for (int h = NW / 2; h >= 1; h >>= 1)
+#pragma unroll
+      for (int w = 0; w < h; ++w) p[w] += p[w + h];
+    atomicAdd(acc + threadIdx.x, p[0]);
   }
 }
 

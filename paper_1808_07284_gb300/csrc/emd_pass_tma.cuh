@@ -268,11 +268,11 @@ __device__ __forceinline__ void flush_gather(const Ctl &c, int g, int n, float (
 // mask (the masked instantiation gives the same values there).  ISO: the isotropic
 // ground cost (vector shrink); a template parameter because a per-cell branch on it cost
 // 5 % of the pass.
-template <int TI, bool INTERIOR, bool ISO>
+template <int TI, bool INTERIOR, bool ISO, int NW = kThreads / 32>
 __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int lane, int warp,
                                           float (&v)[9]) {
   using T = TmaTile<TI>;
-  constexpr int W = T::W, R = T::R, BOX = T::BOX, NW = kThreads / 32;
+  constexpr int W = T::W, R = T::R, BOX = T::BOX;
   constexpr unsigned FULL = 0xffffffffu;
   float *UAx = stg, *UAt = stg + BOX, *UBx = stg + 2 * BOX, *UBt = stg + 3 * BOX;
   float *PH = stg + 4 * BOX, *FF = stg + 5 * BOX;
@@ -329,7 +329,7 @@ __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int l
     st4(PH + o, res);
     if (own && r >= 2 && r < TI + 2 && gi < nr) st4(ph_cur + gi * ntp + gj0, res);
   }
-  compute_sync<true>();
+  compute_sync<true, NW>();
 
   // ---- phase 2: u^{k+1} = shrink(u^k + alpha grad phi^k, alpha) / (1 + eps alpha), rows 1..R-2
 #pragma unroll
@@ -362,7 +362,7 @@ __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int l
       st4(utn + gi * ntp + gj0, nv);
     }
   }
-  compute_sync<true>();
+  compute_sync<true, NW>();
 
   // ---- phase 3: p_k = div u^{k+1} + f -> FF, q_k = div(u^{k+1} - u^k) -> PH, rows 1..R-3
 #pragma unroll
@@ -397,7 +397,7 @@ __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int l
     st4(FF + o, pp);
     st4(PH + o, qq);
   }
-  compute_sync<true>();
+  compute_sync<true, NW>();
 
   // ---- phase 4: the linesearch / residual / distance sums over the tile's own cells
 #pragma unroll
@@ -617,11 +617,12 @@ __device__ __forceinline__ int tile_owner(int t, int total, int grid) {
 // Compute warps: add the CTA's sums over `n` tiles of gather g to the gather's pass-k
 // accumulator set (FP64 reductions in L2), then the tile count with release semantics (it
 // also publishes this CTA's tile stores: the barrier gathers them under thread 0).
+template <int NW>
 __device__ __forceinline__ void flush_gather_persistent(const Ctl &c, int g, int n, int k,
                                                         float (&v)[9]) {
   double *acc = acc_of(c, g, k & 1);
-  block_accumulate<9, true>(v, acc + (blockIdx.x % kSpread) * kAcc);
-  compute_sync<true>();
+  block_accumulate<9, true, NW>(v, acc + (blockIdx.x % kSpread) * kAcc);
+  compute_sync<true, NW>();
   if (threadIdx.x == 0) red_release_add(&c.states[g].tiles_done, static_cast<unsigned>(n));
 #pragma unroll
   for (int q = 0; q < 9; ++q) v[q] = 0.0f;
@@ -647,15 +648,18 @@ __device__ __forceinline__ void warp_totals(const double *acc, double (&out)[9])
   for (int m = 0; m < 9; ++m) out[m] = __shfl_sync(FULL, c[0], m);
 }
 
-template <int TI, int MINB = 2>
-__global__ void __launch_bounds__(kSolveThreads, MINB)
+// NW compute warps, one producer and one decider warp; NS shared-memory stages (the
+// producer keeps up to NS - 1 tiles loading while one is computed).
+template <int TI, int MINB = 2, int NW = kThreads / 32, int NS = 2>
+__global__ void __launch_bounds__((NW + 2) * 32, MINB)
     k_solve_tma(Ctl c, int total_tiles, int max_passes) {
   using T = TmaTile<TI>;
+  constexpr int NT = NW * 32;  // compute threads
   extern __shared__ float4 dyn4[];
   float *sbase = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(dyn4) + 127u) & ~static_cast<uintptr_t>(127u));
-  __shared__ __align__(8) uint64_t full[2], empty[2], gob;
-  __shared__ StageInfo info[2];
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], gob;
+  __shared__ StageInfo info[NS];
   __shared__ int go_flag, hot_gather;
   __shared__ float hot[5];  // alpha, coef, theta, 1/(1+eps alpha), fmean of hot_gather
   __shared__ int hot_done;
@@ -664,16 +668,17 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
   const int t_hi = tile_lo(blockIdx.x + 1, total_tiles, gridDim.x);
 
   if (threadIdx.x == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&empty[0], 1);
-    mbar_init(&empty[1], 1);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
     mbar_init(&gob, 1);
     fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == kThreads / 32 + 1) {  // ---- decider warp: decisions of the gathers this CTA owns
+  if (warp == NW + 1) {  // ---- decider warp: decisions of the gathers this CTA owns
     constexpr unsigned FULL = 0xffffffffu;
     const int g_lo = c.tile_shot[t_lo], g_hi = c.tile_shot[t_hi - 1];
     for (int k = 0; k < max_passes; ++k) {
@@ -709,14 +714,14 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
     return;
   }
 
-  if (warp == kThreads / 32) {  // ---- producer warp: one lane stages every tile of every pass
+  if (warp == NW) {  // ---- producer warp: one lane stages every tile of every pass
     if (lane == 0) {
       int i = 0;
       for (int k = 0; k < max_passes; ++k) {
         bool first = true;
         for (int t = t_lo; t < t_hi; ++t, ++i) {
-          const int s = i & 1;
-          if (i >= 2 && !mbar_wait(&empty[s], ((i - 2) >> 1) & 1)) {
+          const int s = i % NS;
+          if (i >= NS && !mbar_wait(&empty[s], ((i - NS) / NS) & 1)) {
             atomicExch(c.error, 1);
             return;
           }
@@ -773,20 +778,20 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
         mbar_arrive(&gob);
       }
     }
-    compute_sync<true>();
+    compute_sync<true, NW>();
     if (!go_flag) {  // stop: drain the first tile the producer staged for this pass
-      (void)mbar_wait(&full[i & 1], (i >> 1) & 1);
+      (void)mbar_wait(&full[i % NS], (i / NS) & 1);
       return;
     }
     int seg = 0;  // tiles of the current gather summed into v
     for (int t = t_lo; t < t_hi; ++t, ++i) {
-      const int s = i & 1;
-      const bool ok = mbar_wait(&full[s], (i >> 1) & 1);
+      const int s = i % NS;
+      const bool ok = mbar_wait(&full[s], (i / NS) & 1);
       int bad;
       asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 p, %1, 0;\n"
                    " bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
                    : "=r"(bad)
-                   : "r"(static_cast<unsigned>(ok)), "n"(kThreads)
+                   : "r"(static_cast<unsigned>(ok)), "n"(NT)
                    : "memory");
       if (bad) {
         if (threadIdx.x == 0) atomicExch(c.error, 1);
@@ -794,7 +799,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
       }
       StageInfo in = info[s];
       if (in.gather != hot_gather) {  // this pass's step sizes of the tile's gather
-        compute_sync<true>();
+        compute_sync<true, NW>();
         if (threadIdx.x == 0) {
           const State *st = c.states + in.gather;
           const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(st));
@@ -807,7 +812,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
           hot[4] = __int_as_float(h1.z);
           hot_gather = in.gather;
         }
-        compute_sync<true>();
+        compute_sync<true, NW>();
       }
       if (!hot_done) {
         in.alpha = hot[0];
@@ -817,24 +822,24 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
         in.fmean = hot[4];
         if (in.iso) {
           if (in.interior)
-            pass_tile<TI, true, true>(in, sbase + s * T::STAGE, lane, warp, v);
+            pass_tile<TI, true, true, NW>(in, sbase + s * T::STAGE, lane, warp, v);
           else
-            pass_tile<TI, false, true>(in, sbase + s * T::STAGE, lane, warp, v);
+            pass_tile<TI, false, true, NW>(in, sbase + s * T::STAGE, lane, warp, v);
         } else {
           if (in.interior)
-            pass_tile<TI, true, false>(in, sbase + s * T::STAGE, lane, warp, v);
+            pass_tile<TI, true, false, NW>(in, sbase + s * T::STAGE, lane, warp, v);
           else
-            pass_tile<TI, false, false>(in, sbase + s * T::STAGE, lane, warp, v);
+            pass_tile<TI, false, false, NW>(in, sbase + s * T::STAGE, lane, warp, v);
         }
         ++seg;
         const int tn = t + 1;
         const int gn = tn < t_hi ? c.tile_shot[tn] : -1;
         if (gn != in.gather) {
-          flush_gather_persistent(c, in.gather, seg, k, v);
+          flush_gather_persistent<NW>(c, in.gather, seg, k, v);
           seg = 0;
         }
       }
-      compute_sync<true>();                          // every compute warp is done with stage s
+      compute_sync<true, NW>();                      // every compute warp is done with stage s
       if (threadIdx.x == 0) mbar_arrive(&empty[s]);  // hand it back to the producer
     }
   }
