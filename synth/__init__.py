@@ -13,5 +13,6 @@ from .gathers import (  # noqa: F401
     batch_uneven_hyperbolic,
     gather_pair_reflective,
     gather_pair_marine,
+    marine_shot,
     workload,
 )

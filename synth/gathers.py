@@ -221,6 +221,12 @@ def gather_pair_marine(nt=8000, nr=648, dt=2e-3, dx=25.0, f0=5.0, n_refl=40, sho
     return obs.astype(np.float32), pred.astype(np.float32)
 
 
+def marine_shot(shot: int):
+    """gather_pair_marine of one shot with the default geometry (a picklable one-argument
+    form, for generating the 128-shot batch in a process pool)."""
+    return gather_pair_marine(shot=shot)
+
+
 def workload(name: str):
     """Named workloads: returns ``(obs, pred, dt, dx)`` for the single-gather cases."""
     if name == "hyperbolic_256x64":
