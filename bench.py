@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import statistics
@@ -95,11 +96,14 @@ def _peaks():
 
 
 def _kernel_hash():
+    """Hash of the device code of the fused pass (the benchmark gather never takes the
+    resident solve), comments and whitespace removed: a traffic capture stays valid
+    across edits of comments only."""
     h = hashlib.sha256()
-    # the device code of the fused pass (the benchmark gather never takes the resident solve)
     for rel in ("paper_1808_07284_gb300/csrc/emd_kernels.cuh", "paper_1808_07284_gb300/csrc/emd_pass_tma.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, rel)) as fh:
+            code = re.sub(r"//[^\n]*", "", fh.read())
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

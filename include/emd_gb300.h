@@ -46,7 +46,8 @@ typedef enum {
   EMD_ERR_CUDA = 2,       /* a CUDA runtime call failed (launch, copy, sync)             */
   EMD_ERR_NONFINITE = 3,  /* an inner product became NaN/Inf (e.g. NaN in the inputs)    */
   EMD_ERR_LINESEARCH = 4, /* Algorithm 1's backtracking did not pass in ls_max_trials    */
-  EMD_ERR_TIMEOUT = 5,    /* reserved: a bounded device-side wait ran out                */
+  EMD_ERR_TIMEOUT = 5,    /* a bounded device-side wait (4 s) of a persistent solve ran out;
+                             the kernel winds down instead of hanging                    */
   EMD_ERR_WORKSPACE = 6   /* workspace NULL, too small or not 256-byte aligned           */
 } emd_status;
 

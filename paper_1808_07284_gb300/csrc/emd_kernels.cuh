@@ -14,8 +14,9 @@
 //       with six sums that do not depend on a.  One pass therefore settles every
 //       backtracking trial of Algorithm 1 exactly; the trial loop runs on scalars.
 //       The same pass sums the stopping residual and the distance of u^{k+1}.
-// The last CTA of each gather (atomic ticket) reduces the FP64 accumulators and takes
-// the linesearch decision, writing (alpha_{k+1}, theta_{k+1}, c_{k+1}) for pass k+1.
+// In the per-pass kernels the last CTA of each gather (atomic ticket) reduces the FP64
+// accumulators and takes the linesearch decision, writing (alpha_{k+1}, theta_{k+1},
+// c_{k+1}) for pass k+1; the persistent solve (emd_pass_tma.cuh) has a decider warp.
 //
 // Tiles: TI rows (receivers) x TJ = W - 8 columns (time) per CTA, staged in shared
 // memory with a 2-row / 4-column halo on every side (the dependency cone of the three
