@@ -100,8 +100,11 @@ typedef struct {
                         the TMA pass serves the gathers, else graph replays of the pass;
                         1: one plain launch per pass; 2: one launch per pass, replayed
                         from a captured CUDA graph                                       */
-  int debug_fault;   /* fault injection for tests: 0 = off, 1 = every linesearch trial
-                        fails (exercises EMD_ERR_LINESEARCH); never set in production   */
+  int debug_fault;   /* fault injection for tests, never set in production: 0 = off;
+                        1 = every linesearch trial fails (exercises EMD_ERR_LINESEARCH);
+                        2 = the persistent solve never publishes a decision, so its
+                        bounded waits run out after 4 s and it winds down (exercises
+                        EMD_ERR_TIMEOUT; the resident and per-pass paths ignore it)    */
   double *trace;     /* optional per-iteration history, device, B x max_iter x 4 doubles
                         (gather-major): for iteration k, alpha_{k+1}, theta_{k+1}, the
                         linesearch trials it took, and ||div u^{k+1} + f|| / ||f||.

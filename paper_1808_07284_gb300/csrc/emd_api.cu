@@ -167,6 +167,7 @@ bool params_ok(const emd_params &p) {
   if (p.balance != EMD_BAL_NONE && p.balance != EMD_BAL_MEAN) return false;
   if (p.tile < 0 || p.tile > kNumShapes) return false;
   if (p.launch_mode < 0 || p.launch_mode > 2) return false;
+  if (p.debug_fault < 0 || p.debug_fault > 2) return false;
   if (p.norm != EMD_NORM_ANISO && p.norm != EMD_NORM_ISO) return false;
   return true;
 }
@@ -311,6 +312,7 @@ int autotune_shape(int B, const float *const *f_obs, const float *const *f_pred,
     q.tol = 0.0;
     q.launch_mode = 0;  // the persistent solve, which default solves run
     q.trace = nullptr;
+    q.debug_fault = 0;
     if (cudaEventRecord(e0, stream) != cudaSuccess) return -1.0f;
     SolveExtra trial = x;
     trial.finalize = false;

@@ -680,6 +680,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB)
 
   if (warp == NW + 1) {  // ---- decider warp: decisions of the gathers this CTA owns
     constexpr unsigned FULL = 0xffffffffu;
+    if (c.debug_fault == 2) return;  // test hook: no decision is ever published
     const int g_lo = c.tile_shot[t_lo], g_hi = c.tile_shot[t_hi - 1];
     for (int k = 0; k < max_passes; ++k) {
       bool any = false;

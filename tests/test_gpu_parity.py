@@ -324,6 +324,18 @@ def test_linesearch_failure_is_reported(pkg):
     assert g["info"]["iters"] == 0 and g["info"]["ls_trials"] == 40
 
 
+def test_device_wait_timeout_is_reported_and_the_context_survives(pkg):
+    """debug_fault = 2: the persistent solve's decisions are never published, so the
+    compute warps' bounded wait on the decision counter (4 s of %globaltimer) runs out.
+    The solve returns EMD_ERR_TIMEOUT instead of hanging, and the next solve on the same
+    CUDA context is correct."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=600, nr=40, seed=6)
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=50, tile=7, debug_fault=2, check=False)
+    assert g["info"]["status"] == pkg.EMD_ERR_TIMEOUT
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=50)
+    assert_parity(gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=50, tile=7), r)
+
+
 def test_transmissive_full_size_sampled(pkg):
     """The 3000 x 400 gather at full size: same iterates as the oracle after 25 iterations."""
     obs, pred = synth.gather_pair_transmissive()
