@@ -239,25 +239,27 @@ __device__ __forceinline__ void publish(State *st, double eps) {
 }
 
 // What the decision needs besides the pass's sums: loaded and precomputed by the
-// deciding warp while the sums are still being gathered.
+// deciding warp while the sums are still being gathered.  FP64 is slow on this part (a
+// warp instruction occupies the FP64 pipe for 64 cycles whatever its active lanes), so
+// everything that does not depend on the sums is prepared here, per lane: lane t holds
+// trial t's test coefficients and the step sizes (FP64 and FP32) that trial t would
+// accept, and the residual test is prepared in squared form.
 struct DecidePrep {
   double alpha, theta, coef, beta_fixed, fnorm;
   double s_lane, s_lane2, base32;  // sqrt(1 + theta_k) xi^lane, its square, xi^32
   double dak2;                      // delta alpha_k^2
+  double s2x, cl;                   // 2 s_lane; delta alpha_k^2 s_lane^2 / zeta^2
+  double alpha_l, coef_l;           // alpha_k s_lane, delta alpha_k s_lane
+  float alpha_lf, coef_lf, theta_lf, inv_lf;  // their FP32 copies, 1 / (1 + eps alpha)
+  double thr_feas, tol2;            // r_feas <= tol <=> P_pp <= thr_feas; tol^2
   int k;
+  int check;                        // this decision runs the residual test
 };
 
-// St: State (global) or any copy of it with the same field names (shared memory).
-template <typename St>
-__device__ __forceinline__ DecidePrep decide_prep(const Ctl &c, const St *st) {
+// The per-lane part of DecidePrep from its loaded fields (k, alpha, theta, coef,
+// beta_fixed, fnorm).
+__device__ __forceinline__ void decide_prep_lanes(const Ctl &c, DecidePrep &d) {
   const int lane = threadIdx.x & 31;
-  DecidePrep d;
-  d.k = st->k;
-  d.alpha = st->alpha;
-  d.theta = st->theta;
-  d.coef = st->coef;
-  d.beta_fixed = st->beta_fixed;
-  d.fnorm = st->fnorm;
   double xl = 1.0, base = c.xi;  // xl = xi^lane; base ends as xi^32
 #pragma unroll
   for (int b = 0; b < 5; ++b) {
@@ -268,6 +270,30 @@ __device__ __forceinline__ DecidePrep decide_prep(const Ctl &c, const St *st) {
   d.s_lane = sqrt(1.0 + d.theta) * xl;  // upper end of [alpha_k, alpha_k sqrt(1+theta_k)]
   d.s_lane2 = d.s_lane * d.s_lane;
   d.dak2 = c.delta * d.alpha * d.alpha;
+  d.s2x = 2.0 * d.s_lane;
+  d.cl = d.dak2 * d.s_lane2 / (c.zeta * c.zeta);
+  d.alpha_l = d.alpha * d.s_lane;
+  d.coef_l = c.delta * d.alpha_l;
+  d.alpha_lf = static_cast<float>(d.alpha_l);
+  d.coef_lf = static_cast<float>(d.coef_l);
+  d.theta_lf = static_cast<float>(d.s_lane);
+  d.inv_lf = 1.0f / (1.0f + static_cast<float>(c.eps * d.alpha_l));
+  d.check = c.tol > 0.0 && (d.k + 1) % c.check_every == 0;
+  d.tol2 = c.tol * c.tol;
+  d.thr_feas = d.fnorm > 0.0 ? d.tol2 * d.fnorm * d.fnorm : d.tol2;
+}
+
+// St: State (global) or any copy of it with the same field names (shared memory).
+template <typename St>
+__device__ __forceinline__ DecidePrep decide_prep(const Ctl &c, const St *st) {
+  DecidePrep d;
+  d.k = st->k;
+  d.alpha = st->alpha;
+  d.theta = st->theta;
+  d.coef = st->coef;
+  d.beta_fixed = st->beta_fixed;
+  d.fnorm = st->fnorm;
+  decide_prep_lanes(c, d);
   return d;
 }
 
@@ -275,22 +301,31 @@ __device__ __forceinline__ DecidePrep decide_prep(const Ctl &c, const St *st) {
 struct Decision {
   int status, trials_now, k_new;
   bool done, checked;
-  double alpha, theta, coef, r_feas, r_step;
+  double alpha, theta, coef;
+  float alpha_f, coef_f, theta_f, inv_f;  // FP32 copies for the next pass
 };
+
+// True unless x is an infinity or a NaN (integer test of the exponent: no FP64 op).
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
 
 // Linesearch decision of Algorithm 1 from the sums of pass k, taken by one warp.
 // a: 0 P_pp, 1 P_pq, 2 P_qq, 3 G_pp, 4 G_pq, 5 G_qq, 6 sum|u|, 7 sum u^2, 8 sum du^2.
 // Trial t (0-based) uses a = alpha_k s_t with s_t = sqrt(1 + theta_k) xi^t, so the trials
 // do not depend on each other: lane t tests trial t (32 at a time) and a ballot picks the
-// first that passes -- the same choice as Algorithm 1's sequential backtracking.  Then the
-// stopping test (max_iter; the residual every check_every iterations when tol > 0).
+// first that passes -- the same choice as Algorithm 1's sequential backtracking.  The
+// test delta a^2 ||grad(p + s q)||^2 <= zeta^2 ||p + s q||^2 is evaluated as
+// cl (G_pp + 2s G_pq + s^2 G_qq) <= P_pp + 2s P_pq + s^2 P_qq with cl = delta a^2 / zeta^2.
+// Then the stopping test (max_iter; the residual every check_every iterations when
+// tol > 0, compared in squared form: max(r_feas, r_step) <= tol).
 __device__ Decision decide_core(const Ctl &c, const DecidePrep &d, const double (&a_)[9]) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const double Ppp = a_[0], Ppq = a_[1], Pqq = a_[2], Gpp = a_[3], Gpq = a_[4], Gqq = a_[5];
   bool finite = true;  // constant indices keep a_ in registers
 #pragma unroll
-  for (int n = 0; n < 9; ++n) finite = finite && isfinite(a_[n]);
+  for (int n = 0; n < 9; ++n) finite = finite && finite_bits(a_[n]);
   Decision o;
   o.status = ST_OK;
   o.trials_now = 1;
@@ -299,52 +334,81 @@ __device__ Decision decide_core(const Ctl &c, const DecidePrep &d, const double 
   o.alpha = d.alpha;
   o.theta = d.theta;
   o.coef = d.coef;
-  o.r_feas = o.r_step = -1.0;
+  o.alpha_f = o.coef_f = o.theta_f = o.inv_f = 0.0f;
   if (!finite) {
     o.status = ST_NONFINITE;
     o.done = true;
   } else if (c.linesearch) {
-    const double z2 = c.zeta * c.zeta;
-    double s = d.s_lane, s2 = d.s_lane2;
-    int found = -1;
-    double s_found = 0.0;
-    for (int t0 = 0; t0 < c.ls_max_trials && found < 0; t0 += 32) {
-      // delta a^2 ||grad p + s grad q||^2 <= zeta^2 ||p + s q||^2, a = alpha_k s
-      const double lhs = d.dak2 * s2 * (Gpp + s * (2.0 * Gpq + s * Gqq));
-      const double rhs = z2 * (Ppp + s * (2.0 * Ppq + s * Pqq));
-      const bool pass = t0 + lane < c.ls_max_trials && lhs <= rhs && c.debug_fault != 1;
-      const unsigned m = __ballot_sync(FULL, pass);
-      if (m) {
-        const int w = __ffs(m) - 1;
-        found = t0 + w;
-        s_found = __shfl_sync(FULL, s, w);
+    const bool pass0 = lane < c.ls_max_trials && c.debug_fault != 1 &&
+                       d.cl * fma(d.s_lane2, Gqq, fma(d.s2x, Gpq, Gpp)) <=
+                           fma(d.s_lane2, Pqq, fma(d.s2x, Ppq, Ppp));
+    const unsigned m0 = __ballot_sync(FULL, pass0);
+    if (m0) {  // the common case: one of the first 32 trials; its values were prepared
+      const int w = __ffs(m0) - 1;
+      o.trials_now = w + 1;
+      o.theta = __shfl_sync(FULL, d.s_lane, w);
+      o.alpha = __shfl_sync(FULL, d.alpha_l, w);
+      o.coef = __shfl_sync(FULL, d.coef_l, w);
+      o.alpha_f = __shfl_sync(FULL, d.alpha_lf, w);
+      o.coef_f = __shfl_sync(FULL, d.coef_lf, w);
+      o.theta_f = __shfl_sync(FULL, d.theta_lf, w);
+      o.inv_f = __shfl_sync(FULL, d.inv_lf, w);
+    } else {  // trials 32 and beyond, 32 at a time
+      const double b2 = d.base32 * d.base32;
+      double s2x = d.s2x * d.base32, s2 = d.s_lane2 * b2, cl = d.cl * b2;
+      int found = -1;
+      double s_found = 0.0;
+      for (int t0 = 32; t0 < c.ls_max_trials && found < 0; t0 += 32) {
+        const bool pass = t0 + lane < c.ls_max_trials && c.debug_fault != 1 &&
+                          cl * fma(s2, Gqq, fma(s2x, Gpq, Gpp)) <= fma(s2, Pqq, fma(s2x, Ppq, Ppp));
+        const unsigned m = __ballot_sync(FULL, pass);
+        if (m) {
+          const int w = __ffs(m) - 1;
+          found = t0 + w;
+          s_found = 0.5 * __shfl_sync(FULL, s2x, w);
+        }
+        s2x *= d.base32;
+        s2 *= b2;
+        cl *= b2;
       }
-      s *= d.base32;
-      s2 *= d.base32 * d.base32;
-    }
-    if (found >= 0) {
-      o.trials_now = found + 1;
-      o.theta = s_found;
-      o.alpha = d.alpha * s_found;
-      o.coef = c.delta * o.alpha;
-    } else {
-      o.trials_now = c.ls_max_trials;
-      o.status = ST_LINESEARCH;
-      o.done = true;
+      if (found >= 0) {
+        o.trials_now = found + 1;
+        o.theta = s_found;
+        o.alpha = d.alpha * s_found;
+        o.coef = c.delta * o.alpha;
+        o.alpha_f = static_cast<float>(o.alpha);
+        o.coef_f = static_cast<float>(o.coef);
+        o.theta_f = static_cast<float>(o.theta);
+        o.inv_f = 1.0f / (1.0f + static_cast<float>(c.eps * o.alpha));
+      } else {
+        o.trials_now = c.ls_max_trials;
+        o.status = ST_LINESEARCH;
+        o.done = true;
+      }
     }
   } else {
     o.coef = d.beta_fixed;
     o.theta = 1.0;
+    o.alpha_f = static_cast<float>(o.alpha);
+    o.coef_f = static_cast<float>(o.coef);
+    o.theta_f = 1.0f;
+    o.inv_f = 1.0f / (1.0f + static_cast<float>(c.eps * o.alpha));
   }
   o.k_new = o.status == ST_OK ? d.k + 1 : d.k;
   if (!o.done && o.k_new >= c.max_iter) o.done = true;
-  if (!o.done && c.tol > 0.0 && o.k_new % c.check_every == 0) {
+  if (!o.done && d.check) {
     o.checked = true;
-    o.r_feas = d.fnorm > 0.0 ? sqrt(Ppp) / d.fnorm : sqrt(Ppp);
-    o.r_step = sqrt(a_[8]) / fmax(sqrt(a_[7]), 1e-30);
-    if (fmax(o.r_feas, o.r_step) <= c.tol) o.done = true;
+    if (Ppp <= d.thr_feas && a_[8] <= d.tol2 * fmax(a_[7], 1e-60)) o.done = true;
   }
   return o;
+}
+
+// The reported residuals of a checked decision (Q6): r_feas = ||div u + f|| / ||f||,
+// r_step = ||du|| / ||u||.  Not on the decision's critical path.
+__device__ __forceinline__ void residuals(const DecidePrep &d, const double (&a_)[9],
+                                          double &r_feas, double &r_step) {
+  r_feas = d.fnorm > 0.0 ? sqrt(a_[0]) / d.fnorm : sqrt(a_[0]);
+  r_step = sqrt(a_[8]) / fmax(sqrt(a_[7]), 1e-30);
 }
 
 // One entry of the optional per-iteration history (lane 0 of the deciding warp).
@@ -374,15 +438,15 @@ __device__ void decide(const Ctl &c, State *st, const DecidePrep &d, const doubl
     st->theta = o.theta;
     st->coef = o.coef;
     st->k = o.k_new;
-    publish(st, c.eps);
+    st->alpha_f = o.alpha_f;
+    st->coef_f = o.coef_f;
+    st->theta_f = o.theta_f;
+    st->inv_f = o.inv_f;
   } else {
     st->status = o.status;
   }
   write_trace(c, gather, d.k, o, a_[0], d.fnorm);
-  if (o.checked) {
-    st->r_feas = o.r_feas;
-    st->r_step = o.r_step;
-  }
+  if (o.checked) residuals(d, a_, st->r_feas, st->r_step);
   if (o.done) {
     st->done = 1;
     atomicAdd(c.n_done, 1);

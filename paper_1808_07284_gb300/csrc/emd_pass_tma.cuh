@@ -588,12 +588,13 @@ __device__ __forceinline__ bool wait_count(const unsigned *counter, unsigned tar
 
 // Decider warp: decision k of gather g from its totals, written to the global state from
 // registers only (no read of what was just stored: a global load here is a round trip on
-// the critical path).  `trials` is the warp's running trial count of the gather.
-__device__ __forceinline__ void decide_publish(const Ctl &c, State *st, const DecidePrep &pr,
-                                               const double (&a_)[9], int g, int &trials) {
+// the critical path).  `trials` is the warp's running trial count of the gather.  The
+// reported residuals are left to the caller, after the release.
+__device__ __forceinline__ Decision decide_publish(const Ctl &c, State *st, const DecidePrep &pr,
+                                                   const double (&a_)[9], int g, int &trials) {
   const Decision o = decide_core(c, pr, a_);
   trials += o.trials_now;
-  if ((threadIdx.x & 31) != 0) return;
+  if ((threadIdx.x & 31) != 0) return o;
   st->s_p2 = a_[0];
   st->s_u1 = a_[6];
   st->s_u2 = a_[7];
@@ -604,22 +605,19 @@ __device__ __forceinline__ void decide_publish(const Ctl &c, State *st, const De
     st->theta = o.theta;
     st->coef = o.coef;
     st->k = o.k_new;
-    st->alpha_f = static_cast<float>(o.alpha);
-    st->coef_f = static_cast<float>(o.coef);
-    st->theta_f = static_cast<float>(o.theta);
-    st->inv_f = 1.0f / (1.0f + static_cast<float>(c.eps * o.alpha));
+    st->alpha_f = o.alpha_f;
+    st->coef_f = o.coef_f;
+    st->theta_f = o.theta_f;
+    st->inv_f = o.inv_f;
   } else {
     st->status = o.status;
   }
   write_trace(c, g, pr.k, o, a_[0], pr.fnorm);
-  if (o.checked) {
-    st->r_feas = o.r_feas;
-    st->r_step = o.r_step;
-  }
   if (o.done) {
     st->done = 1;
     atomicAdd(c.n_done, 1);
   }
+  return o;
 }
 
 // The CTA that owns tile t when CTA b of `grid` owns [tile_lo(b), tile_lo(b + 1)): the
@@ -642,24 +640,28 @@ __device__ __forceinline__ void flush_gather_persistent(const Ctl &c, int g, int
   for (int q = 0; q < 9; ++q) v[q] = 0.0f;
 }
 
-// Decider warp: the totals of a gather's kSpread accumulator copies.  Lane n < 9 loads
-// the copies of value n and sums them pairwise in registers (four dependent FP64 adds, no
-// shuffles); one shuffle per value then gives every lane all nine.  Lanes past 8 repeat
-// value 0, so control flow stays uniform.
+// Decider warp: the totals of a gather's kSpread accumulator copies.  Lanes 2n and 2n + 1
+// (n < 9) each load half of the copies of value n and sum them pairwise in registers, one
+// exchange adds the two halves, and one shuffle per value then gives every lane all nine:
+// 8 warp-wide FP64 adds on the critical path instead of 15 (each occupies the FP64 pipe
+// for 64 cycles, whatever its active lanes).  Lanes past 17 repeat value 0, so control
+// flow stays uniform.
 __device__ __forceinline__ void warp_totals(const double *acc, double (&out)[9]) {
-  static_assert((kSpread & (kSpread - 1)) == 0, "pairwise sum over a power of two");
+  constexpr int H = kSpread / 2;
+  static_assert(kSpread % 2 == 0 && (H & (H - 1)) == 0, "pairwise sum over a power of two");
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int n = lane < 9 ? lane : 0;
-  double c[kSpread];
+  const int n = lane < 18 ? lane >> 1 : 0, h = lane & 1;
+  double c[H];
 #pragma unroll
-  for (int q = 0; q < kSpread; ++q) c[q] = __ldcg(acc + q * kAcc + n);
+  for (int q = 0; q < H; ++q) c[q] = __ldcg(acc + (h * H + q) * kAcc + n);
 #pragma unroll
-  for (int w = kSpread / 2; w >= 1; w >>= 1)
+  for (int w = H / 2; w >= 1; w >>= 1)
 #pragma unroll
     for (int q = 0; q < w; ++q) c[q] += c[q + w];
+  c[0] += __shfl_xor_sync(FULL, c[0], 1);
 #pragma unroll
-  for (int m = 0; m < 9; ++m) out[m] = __shfl_sync(FULL, c[0], m);
+  for (int m = 0; m < 9; ++m) out[m] = __shfl_sync(FULL, c[0], 2 * m);
 }
 
 // NW compute warps, one producer and one decider warp; NS shared-memory stages (the
@@ -716,9 +718,12 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB)
         double a_[9];
         double *acc = acc_of(c, g, k & 1);
         warp_totals(acc, a_);
-        decide_publish(c, st, pr, a_, g, trials);
+        const Decision o = decide_publish(c, st, pr, a_, g, trials);
         __syncwarp();  // the new state, before the release
-        if (lane == 0) st_release(&st->epoch, static_cast<unsigned>(k + 1));
+        if (lane == 0) {
+          st_release(&st->epoch, static_cast<unsigned>(k + 1));
+          if (o.checked) residuals(pr, a_, st->r_feas, st->r_step);
+        }
         // pass k + 2 adds into this set again; the release of epoch k + 2 (after decision
         // k + 1) orders these zeros before any of its flushes
 #pragma unroll

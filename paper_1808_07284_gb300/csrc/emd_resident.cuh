@@ -94,18 +94,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_solve_resident(Ctl c) {
       for (int q = tid; q < N; q += NT) PH[q] += coef * (PP[q] + theta * QQ[q]);
     } else {
       // the decision warp: this pass's decision inputs, while the cells are worked on
-      const int l = lane;
-      double xl = 1.0, base = c.xi;
-#pragma unroll
-      for (int b = 0; b < 5; ++b) {
-        if ((l >> b) & 1) xl *= base;
-        base *= base;
-      }
       pr = dp;
-      pr.base32 = base;
-      pr.s_lane = sqrt(1.0 + pr.theta) * xl;
-      pr.s_lane2 = pr.s_lane * pr.s_lane;
-      pr.dak2 = c.delta * pr.alpha * pr.alpha;
+      decide_prep_lanes(c, pr);
     }
     __syncthreads();
     if (worker) {
@@ -189,17 +179,14 @@ __global__ void __launch_bounds__(kResThreads, 1) k_solve_resident(Ctl c) {
           dp.alpha = o.alpha;
           dp.theta = o.theta;
           dp.coef = o.coef;
-          sc[0] = static_cast<float>(o.alpha);
-          sc[1] = static_cast<float>(o.coef);
-          sc[2] = static_cast<float>(o.theta);
-          sc[3] = 1.0f / (1.0f + static_cast<float>(c.eps * o.alpha));
+          sc[0] = o.alpha_f;
+          sc[1] = o.coef_f;
+          sc[2] = o.theta_f;
+          sc[3] = o.inv_f;
         } else {
           sstatus = o.status;
         }
-        if (o.checked) {
-          st->r_feas = o.r_feas;
-          st->r_step = o.r_step;
-        }
+        if (o.checked) residuals(pr, a_, st->r_feas, st->r_step);
         sdone = o.done;
       }
     }
