@@ -628,12 +628,24 @@ __device__ __forceinline__ int tile_owner(int t, int total, int grid) {
 
 // Compute warps: add the CTA's sums over `n` tiles of gather g to the gather's pass-k
 // accumulator set (FP64 reductions in L2), then the tile count with release semantics (it
-// also publishes this CTA's tile stores: the barrier gathers them under thread 0).
+// also publishes this CTA's tile stores and sums: the barrier gathers them under thread
+// 0).  Each warp adds its own FP32 totals (lane q holds value q) to one of the kSpread
+// FP64 copies: one conversion and one reduction per warp, and no block-wide FP64 sum
+// (whose eight conversions and seven adds, at 64 cycles of the FP64 pipe each, sat on
+// the critical path of every pass).
 template <int NW>
 __device__ __forceinline__ void flush_gather_persistent(const Ctl &c, int g, int n, int k,
                                                         float (&v)[9]) {
   double *acc = acc_of(c, g, k & 1);
-  block_accumulate<9, true, NW>(v, acc + (blockIdx.x % kSpread) * kAcc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float mine = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const float w = warp_sum(v[q]);
+    if (lane == q) mine = w;
+  }
+  if (lane < 9)
+    atomicAdd(acc + ((blockIdx.x * NW + warp) % kSpread) * kAcc + lane, static_cast<double>(mine));
   compute_sync<true, NW>();
   if (threadIdx.x == 0) red_release_add(&c.states[g].tiles_done, static_cast<unsigned>(n));
 #pragma unroll
