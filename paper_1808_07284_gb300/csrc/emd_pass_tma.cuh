@@ -410,15 +410,11 @@ __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int l
     const int gi = i0 - 2 + r;
     const bool xl = ROWS_IN || gi > 0;
     const int o = r * W + 4 * lane;
-    float pp[4], pu[4], qq[4], qu[4], nx[4], nv[4], bx[4], bt[4];
+    float pp[4], pu[4], qq[4], qu[4];
     ld4(FF + o, pp);
     ld4(FF + o - W, pu);
     ld4(PH + o, qq);
     ld4(PH + o - W, qu);
-    ld4(UAx + o, nx);
-    ld4(UAt + o, nv);
-    ld4(UBx + o, bx);
-    ld4(UBt + o, bt);
     const float pL = __shfl_up_sync(FULL, pp[3], 1), qL = __shfl_up_sync(FULL, qq[3], 1);
     if (own && gi < nr) {
 #pragma unroll
@@ -434,7 +430,16 @@ __device__ __forceinline__ void pass_tile(const StageInfo &in, float *stg, int l
         v[3] += gpx * gpx + gpt * gpt;
         v[4] += gpx * gqx + gpt * gqt;
         v[5] += gqx * gqx + gqt * gqt;
-        if (need_res) {  // sum |u| is left to the finalize pass, which recomputes it
+      }
+      if (need_res) {  // sum |u| is left to the finalize pass, which recomputes it
+        float nx[4], nv[4], bx[4], bt[4];
+        ld4(UAx + o, nx);
+        ld4(UAt + o, nv);
+        ld4(UBx + o, bx);
+        ld4(UBt + o, bt);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (!cin[q]) continue;
           const float dx_ = nx[q] - bx[q], dt_ = nv[q] - bt[q];
           v[7] += nx[q] * nx[q] + nv[q] * nv[q];
           v[8] += dx_ * dx_ + dt_ * dt_;
