@@ -310,6 +310,27 @@ def test_batched_with_tolerance_stops_each_gather(pkg):
         assert abs(its[b] - r["iters"]) <= 0.2 * r["iters"]
 
 
+@pytest.mark.parametrize("nt,nr,gpu_kw", [
+    (300, 24, {}),                   # persistent TMA solve (decider warp)
+    (300, 24, dict(launch_mode=1)),  # per-pass launches (last CTA decides)
+    (256, 16, {}),                   # whole solve in one CTA's shared memory
+])
+def test_backtracking_past_32_trials(pkg, nt, nr, gpu_kw):
+    """An initial step 1000 / sqrt(delta lambda) with xi = 0.9: the first decision takes 45
+    trials in the oracle's sequential backtracking, so the deciding warp's first round of
+    32 lane-parallel trials (whose step sizes are prepared per lane) all fail and the
+    second round, evaluated from the scaled coefficients, must pick the same trial.  The
+    later decisions take 1-25 trials.  Element parity up to the first near tie."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=nt, nr=nr, seed=9)
+    dt, dx = 2e-3, 10.0
+    lam = 4.0 / dx ** 2 + 4.0 / dt ** 2
+    kw = dict(alpha0=1000.0 / math.sqrt(1e5 * lam), xi=0.9, ls_max_trials=120)
+    first = O.pdhg(obs, pred, dt, dx, max_iter=1, record=True, **kw)
+    assert int(first["trace"][0, 2]) > 32
+    k = parity_until_first_flip(pkg, obs, pred, dt, dx, 60, gpu_kw=gpu_kw, **kw)
+    assert k >= 10
+
+
 def test_nan_input_reports_nonfinite(pkg):
     obs, pred = synth.gather_pair_hyperbolic(nt=64, nr=8)
     pred[3, 10] = np.nan
