@@ -11,8 +11,15 @@
 //    (float4 shared-memory access); the j +- 1 neighbours at lane boundaries come from the
 //    adjacent lanes by warp shuffles, the i +- 1 neighbours from the rows above / below.
 //  * A CTA accumulates its sums over all its tiles of a gather and flushes them once
-//    (FP32 within the warp, FP64 above), adding its tile count to the gather's ticket;
-//    the CTA that completes the count takes the linesearch decision.
+//    (FP32 within the warp, FP64 above).  In the per-pass kernel (k_pass_tma) it adds its
+//    tile count to the gather's ticket and the CTA that completes the count takes the
+//    linesearch decision; in the persistent solve (k_solve_tma) every pass runs inside one
+//    launch, each warp adds its totals to the accumulators, and a decider warp of the
+//    CTA that owns the gather's first tile waits for the cumulative tile count, decides
+//    and publishes the step sizes of the next pass (an epoch counter that the other CTAs
+//    wait on).
+//  * A tile runs one of three instantiations by edge class: no masks, column steps
+//    without masks (tiles at the top or bottom of a gather), or fully masked.
 //
 // Tile: TI receivers x 120 time samples; staged box (TI + 4) x 128 with the halo of 2
 // rows and 4 columns.  Lanes 1..30 own the 120 output columns; lanes 0 and 31 only
