@@ -1,0 +1,35 @@
+"""The benchmark's reference arm (the FP64 oracle on the host cores) keeps the JSON-line
+contract: one line on stdout with the metric, the value and the keys the driver reads.
+Runs on CPU; the GPU arm's line is produced on a GPU machine."""
+
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run(
+        [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+         "--warmup", "1"],
+        cwd=ROOT, capture_output=True, text=True, timeout=600, check=True)
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    r = json.loads(lines[0])
+    assert r["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in r, key
+    assert r["value"] > 0 and r["unit"] == "cell-updates/s" and r["higher_is_better"] is True
+    assert r["steps"] == 1 and r["warmup"] == 1 and r["n_gpus"] == 1
+    assert r["dtype"] == "f64" and r["vs_baseline"] is None
+    assert "workload" in r["config"]
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["value"] == r["value"]
+    e2e = r["e2e"]
+    assert e2e["value"] == r["value"] and e2e["unit"] == r["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
