@@ -72,6 +72,12 @@ class Params:
     norm: int = NORM_ANISO
     phi_init: np.ndarray | None = field(default=None, repr=False)
     m_init: np.ndarray | None = field(default=None, repr=False)
+    # Replay input (test infrastructure, not part of the method): when given, iteration k
+    # runs exactly force_trials[k] linesearch trials and accepts the last one, whatever
+    # its own test says; the test is still evaluated and every trial on which it disagrees
+    # with the forced outcome is recorded (trace column 6).  Used to follow the decisions
+    # another implementation took at near ties and compare the iterates afterwards.
+    force_trials: np.ndarray | None = field(default=None, repr=False)
 
 
 # --------------------------------------------------------------------------- decomposition
@@ -254,10 +260,12 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
 
     Returns a dict with dist, dist_l1, phi, ux, ut, iters, trials, status, residual,
     r_feas, r_step, alpha, theta, imbalance, gap (and a per-iteration ``trace`` when
-    ``record`` is set: alpha, theta, trials, r_feas, r_step, and the smallest relative gap
+    ``record`` is set: alpha, theta, trials, r_feas, r_step, the smallest relative gap
     |lhs - rhs| / rhs between the two sides of the linesearch test over the iteration's
     trials -- a near tie there is where a computation in other precision may decide
-    differently).
+    differently -- and, with ``force_trials``, the largest relative gap among the trials
+    whose own test outcome contradicts the forced one, 0 when the forced count is the
+    test's own choice).
     """
     p = params if params is not None else Params()
     if kw:
@@ -294,12 +302,18 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
     iters = 0
     r_feas = r_step = math.inf
     trace = []
+    forced = None if p.force_trials is None else np.asarray(p.force_trials, np.int64)
+    if forced is not None and p.linesearch:
+        if forced.size < p.max_iter or (forced[:p.max_iter] < 1).any():
+            raise ValueError("force_trials needs a count >= 1 for each of the max_iter iterations")
     for k in range(p.max_iter):
         nux, nut = primal_step(ux, ut, phi, alpha, p.eps, dt, dx, p.norm)
+        disagree = 0.0
         if p.linesearch:
             a = alpha * math.sqrt(1.0 + theta)
             accepted = False
             margin = math.inf  # closest any trial of this iteration came to the test's threshold
+            want = None if forced is None else int(forced[k])
             for trial in range(1, p.ls_max_trials + 1):
                 th = a / alpha
                 beta = p.delta * a
@@ -311,9 +325,14 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
                 trials_total += 1
                 lhs = math.sqrt(p.delta) * a * _norm_vec(gdx, gdt, p.ls_norm)
                 rhs = p.zeta * _norm_scalar(dphi, p.ls_norm)
-                if rhs > 0:
-                    margin = min(margin, abs(lhs - rhs) / rhs)
-                if lhs <= rhs:
+                gap = abs(lhs - rhs) / rhs if rhs > 0 else math.inf
+                margin = min(margin, gap)
+                passed = lhs <= rhs
+                if want is not None:  # replay: the forced count decides, the test is recorded
+                    if passed != (trial == want):
+                        disagree = max(disagree, gap)
+                    passed = trial == want
+                if passed:
                     accepted = True
                     break
                 a = p.xi * a
@@ -335,7 +354,7 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
         ux, ut, phi = nux, nut, nphi
         iters = k + 1
         if record:
-            trace.append((alpha, theta, trial, r_feas, r_step, margin))
+            trace.append((alpha, theta, trial, r_feas, r_step, margin, disagree))
         if not (np.isfinite(phi).all() and np.isfinite(ux).all() and np.isfinite(ut).all()):
             status = STATUS_NONFINITE
             break

@@ -300,3 +300,77 @@ def test_lsd_misfit_and_adjoint():
     p2[1, 7] -= h
     fd = (O.lsd_misfit(obs, p1, 2e-3, 10.0)[0] - O.lsd_misfit(obs, p2, 2e-3, 10.0)[0]) / (2 * h)
     assert fd == pytest.approx(g[1, 7], rel=1e-6, abs=1e-12)
+
+
+def test_stopping_residual_hand_worked():
+    """Reading Q6's residual on the 1x3 fixture above, run with mean balancing: the raw
+    difference Pcal - Pobs = [0, 1, 2] has mean 1, so the balanced f is [-1, 0, 1] and
+    the iterates are the hand-worked ones.  By hand: u^1 = u^2 = 0, so r_feas = ||f|| /
+    ||f|| = 1 and r_step = 0 / tiny = 0; u^3_t = c at j = 1, 2 gives div u^3 + f =
+    (1 - c) [-1, 0, 1], so r_feas = |1 - c|, and r_step = ||u^3|| / ||u^3|| = 1.  A norm
+    of the unbalanced f (sqrt 5) or a dropped square root fails this."""
+    obs = np.array([[1.0, 0.0, 0.0]])
+    pred = np.array([[1.0, 1.0, 2.0]])
+    a1 = 0.5 * math.sqrt(2.0)
+    a2 = 0.5 * a1 * math.sqrt(1.0 + a1 / 0.5)
+    c = a2 * (a1 + a2 - 1.0)
+    r = O.pdhg(obs, pred, 1.0, 1.0, max_iter=3, eps=0.0, delta=1.0, balance=O.BAL_MEAN, record=True)
+    tr = r["trace"]
+    np.testing.assert_array_equal(tr[:, 2], [1, 2, 1])
+    np.testing.assert_allclose(tr[:, 3], [1.0, 1.0, 1.0 - c], rtol=1e-14)
+    np.testing.assert_array_equal(tr[:, 4], [0.0, 0.0, 1.0])
+    assert r["r_feas"] == pytest.approx(1.0 - c, rel=1e-14)
+    assert r["r_step"] == 1.0 and r["residual"] == 1.0
+    # the stopping test reads the same values: tol between them stops at the third check
+    s = O.pdhg(obs, pred, 1.0, 1.0, max_iter=50, eps=0.0, delta=1.0, tol=1.0, check_every=3)
+    assert s["iters"] == 3
+
+
+def test_linesearch_l1_norm_hand_worked():
+    """The printed l1 form of the linesearch test (reading Q3, ls_norm = 1) on a 1x3 grid,
+    dt = 1, f = [-1, 1, 0], eps = 0, delta = 1, xi = 0.9, no balancing; one iteration by
+    hand.  u^1 = 0 (phi^0 = 0), so the trial potential is a f and its time gradient
+    a [0, 2, -1]: the l1 test reads a * 3a <= 0.99 * 2a (a <= 0.66), the Euclidean one
+    a sqrt(5) a <= 0.99 sqrt(2) a (a <= 0.6261).  Trials a = 0.7071, 0.6364, 0.5728: l1
+    accepts the second, l2 the third."""
+    obs = np.array([[1.0, 0.0, 0.0]])
+    pred = np.array([[0.0, 1.0, 0.0]])
+    f = np.array([-1.0, 1.0, 0.0])
+    kw = dict(max_iter=1, eps=0.0, delta=1.0, xi=0.9, balance=O.BAL_NONE, record=True)
+    a0 = 0.5 * math.sqrt(2.0)
+    for ls_norm, trials in ((1, 2), (2, 3)):
+        r = O.pdhg(obs, pred, 1.0, 1.0, ls_norm=ls_norm, **kw)
+        a = a0 * 0.9 ** (trials - 1)
+        assert r["trials"] == trials
+        assert r["alpha"] == pytest.approx(a, rel=1e-14)
+        assert r["theta"] == pytest.approx(a / 0.5, rel=1e-14)
+        np.testing.assert_allclose(r["phi"][0], a * f, rtol=1e-14)
+        np.testing.assert_array_equal(r["ut"], 0.0)
+
+
+def test_forced_trials_replay_is_bit_identical():
+    """Replaying the oracle's own trial counts reproduces its run bit for bit, with no
+    recorded disagreement; forcing one more trial at an iteration whose first trial
+    passed records that trial's gap and takes one more backtracking step there."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=48, nr=6, dt=4e-3)
+    kw = dict(max_iter=200, record=True)
+    r = O.pdhg(obs, pred, 4e-3, 10.0, **kw)
+    tr = r["trace"]
+    assert tr[:, 2].max() > 1
+    q = O.pdhg(obs, pred, 4e-3, 10.0, force_trials=tr[:, 2].astype(int), **kw)
+    for key in ("phi", "ux", "ut"):
+        np.testing.assert_array_equal(q[key], r[key])
+    np.testing.assert_array_equal(q["trace"][:, :6], tr[:, :6])
+    np.testing.assert_array_equal(q["trace"][:, 6], 0.0)
+    assert q["dist"] == r["dist"] and q["trials"] == r["trials"]
+    k = int(np.nonzero(tr[:, 2] == 1)[0][5])
+    forced = tr[:, 2].astype(int).copy()
+    forced[k] = 2
+    s = O.pdhg(obs, pred, 4e-3, 10.0, force_trials=forced, **kw)
+    st = s["trace"]
+    np.testing.assert_array_equal(st[:k], tr[:k])
+    assert st[k, 2] == 2 and st[k, 6] == pytest.approx(tr[k, 5], rel=1e-12)
+    a_prev = tr[k - 1, 0] if k > 0 else 1.0 / math.sqrt(1e5 * O.lambda_bound(6, 4e-3, 10.0))
+    th_prev = tr[k - 1, 1] if k > 0 else 1.0
+    assert st[k, 0] == pytest.approx(a_prev * math.sqrt(1.0 + th_prev) * 0.5, rel=1e-14)
+    assert not np.array_equal(s["phi"], r["phi"])
