@@ -173,9 +173,12 @@ emd_status emd_dyn_solve(const float *f_obs, const float *f_pred, int nt, int nr
 size_t emd_batched_workspace_size(int B, const int *nt, const int *nr);
 
 /*
- * B independent solves (the paper solves one EMD per shot) in one launch per PDHG
- * iteration over all gathers, each gather with its own linesearch state; gathers
- * that meet tol stop while the rest go on.  All arrays of pointers and sizes are HOST
+ * B independent solves (the paper solves one EMD per shot), each gather with its own
+ * linesearch state; gathers that meet tol stop while the rest go on.  How the passes are
+ * launched follows params->launch_mode as for emd_dyn_solve: by default (0) one persistent
+ * cooperative launch runs every PDHG iteration of every gather (gathers of at most 7168
+ * cells each get one shared-memory-resident CTA instead); 1 issues one launch per
+ * iteration over all gathers, 2 replays those launches from a captured CUDA graph.  All arrays of pointers and sizes are HOST
  * arrays of length B; the pointers they hold are device pointers with the layouts of
  * emd_dyn_solve.  params apply to every gather (its warm-start pointers must be NULL).
  * results: HOST array of B.  Returns EMD_OK if every gather succeeded, else the first
@@ -198,23 +201,46 @@ emd_status emd_adjoint(const float *phi, int nt, int nr, double dt, double dx, i
                        const float *grad_out, float *grad_pred, float *grad_obs,
                        void *workspace, size_t ws_bytes, emd_stream_t stream);
 
+/* Bytes of workspace emd_adjoint_batched needs for B gathers (0 if B < 1). */
+size_t emd_batched_adjoint_workspace_size(int B);
+
+/*
+ * Adjoint sources of B gathers at once (Sec. 2.3, as emd_adjoint for each gather): one
+ * launch sums every gather's phi (balance == EMD_BAL_MEAN), one launch scales them.
+ * phi, grad_pred: HOST arrays of B device pointers ([nr[b]][nt[b]] each, FP32); grad_obs:
+ * HOST array of B device pointers or NULL (entries may be NULL); nt, nr, dt, dx: HOST
+ * arrays of B.  grad_out: device array of B FP32 upstream gradients, NULL meaning 1 for
+ * every gather.  Workspace: emd_batched_adjoint_workspace_size(B) bytes (device, 256-byte
+ * aligned).  Does not synchronise.
+ */
+emd_status emd_adjoint_batched(int B, const float *const *phi, const int *nt, const int *nr,
+                               const double *dt, const double *dx, int balance,
+                               const float *grad_out, float *const *grad_pred,
+                               float *const *grad_obs, void *workspace, size_t ws_bytes,
+                               emd_stream_t stream);
+
 /*
  * emd_dyn_solve without a workspace argument, for callers that cannot allocate device
- * memory: code running during stream capture into a CUDA graph, code whose framework
- * allocator owns all device memory, or loops that must never block on an allocation.
- * The paper has no counterpart; this is a deployment convenience.
+ * memory: code whose host framework owns every device allocation (a custom allocator or
+ * a fixed memory budget), real-time loops that must never block on an allocation, or
+ * plug-ins that are handed only input and output buffers.  The paper has no counterpart;
+ * this is a deployment convenience.
  *
  * Scratch space is a 16 MiB array compiled into the library (every GPU that loads the
  * library holds it until the process exits), so the gather must satisfy
  * emd_workspace_size(nt, nr) <= 16 MiB (about 450k cells, e.g. 1024 x 400); larger
  * gathers return EMD_ERR_WORKSPACE without launching anything.  Arguments, outputs and
- * results are those of emd_dyn_solve; the passes run as plain kernel launches (no CUDA
- * graph is instantiated) and nothing calls cudaMalloc or cudaFree.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress with that device
- * current); make that first call before any stream capture.  Every call on a device
- * shares the one array, which keeps the last call's contents (each call re-initialises
- * what it needs): calls that overlap on the GPU (different streams, or different host
- * threads without ordering) race and give wrong results.
+ * results are those of emd_dyn_solve, with two differences: tile = 0 takes the library's
+ * default tile shape without the autotuner's timed trial solves, and no CUDA graph is
+ * captured (launch_mode 0 runs the shared-memory or the persistent cooperative solve and,
+ * where neither can be launched, one plain launch per pass; launch_mode 2 is run as 1).
+ * Nothing calls cudaMalloc or cudaFree.  Like emd_dyn_solve the call copies small host
+ * tables to the device and synchronises `stream` to read the result back.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress with that device
+ * current).  Every call on a device shares the one array, which keeps the last call's
+ * contents (each call re-initialises what it needs): calls that overlap on the GPU
+ * (different streams, or different host threads without ordering) race and give wrong
+ * results.
  */
 emd_status emd_dyn_solve_noalloc(const float *f_obs, const float *f_pred, int nt, int nr,
                                  double dt, double dx, const emd_params *params, float *phi,

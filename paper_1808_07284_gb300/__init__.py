@@ -16,7 +16,8 @@ from __future__ import annotations
 from ._binding import (  # noqa: F401
     EMD_BAL_MEAN, EMD_BAL_NONE, EMD_ERR_ARG, EMD_NORM_ANISO, EMD_NORM_ISO, EMD_ERR_CUDA, EMD_ERR_LINESEARCH,
     EMD_ERR_NONFINITE, EMD_ERR_TIMEOUT, EMD_ERR_WORKSPACE, EMD_OK, EXPORTS,
-    EmdError, EmdMgParams, EmdParams, EmdResult, emd_adjoint, emd_batched_mg_workspace_size,
+    EmdError, EmdMgParams, EmdParams, EmdResult, emd_adjoint, emd_adjoint_batched,
+    emd_batched_adjoint_workspace_size, emd_batched_mg_workspace_size,
     emd_batched_workspace_size, emd_decompose, emd_default_mg_params, emd_default_params,
     emd_dyn_solve, emd_dyn_solve_batched, emd_dyn_solve_batched_mg, emd_dyn_solve_mg,
     emd_dyn_solve_noalloc, emd_lsd, emd_mg_workspace_size, emd_prolong_time, emd_restrict_time,
@@ -29,7 +30,7 @@ __all__ = [
     "emd_batched_workspace_size", "emd_status_string", "emd_tile_count", "EmdError",
     "emd_dyn_solve_mg", "emd_dyn_solve_batched_mg", "emd_default_mg_params", "emd_mg_workspace_size",
     "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time", "emd_lsd", "lsd_loss",
-    "LSDFunction",
+    "LSDFunction", "emd_adjoint_batched", "emd_batched_adjoint_workspace_size",
 ]
 
 
@@ -64,7 +65,8 @@ def emd(f_obs, f_pred, dt, dx, workspace=None, stream=None, check=True, multigri
 
 def emd_batched(f_obs, f_pred, dts, dxs, workspace=None, stream=None, check=True, multigrid=None,
                 **params):
-    """B independent solves in one launch per iteration.  Lists in, lists out:
+    """B independent solves together (by default one persistent launch runs every PDHG
+    iteration of every gather, each gather with its own linesearch).  Lists in, lists out:
     ``(dists, phis, ms, infos)``.  ``multigrid`` as for :func:`emd` (both stages batched)."""
     import torch
     B = len(f_obs)
@@ -145,16 +147,11 @@ def _batched_autograd_function():
             phis = ctx.saved_tensors
             B = len(phis)
             g = grad_out.detach().to(torch.float32).contiguous()
-            gps, gos = [], []
-            for b, phi in enumerate(phis):
-                nr, nt = phi.shape
-                gp = torch.empty_like(phi)
-                go = torch.empty_like(phi)
-                ws = new_workspace(emd_workspace_size(nt, nr), phi.device)
-                emd_adjoint(phi, ctx.dts[b], ctx.dxs[b], ctx.balance, g[b:b + 1], gp, go, ws)
-                gps.append(gp)
-                gos.append(go)
-            return (None, None, None, *gps, *gos)
+            gps = [torch.empty_like(phi) for phi in phis]
+            gos = [torch.empty_like(phi) for phi in phis] if ctx.needs_input_grad[3 + B] else None
+            ws = new_workspace(emd_batched_adjoint_workspace_size(B), phis[0].device)
+            emd_adjoint_batched(list(phis), ctx.dts, ctx.dxs, ctx.balance, g, gps, gos, ws)
+            return (None, None, None, *gps, *(gos if gos is not None else [None] * B))
 
     return EMDBatchFunction
 

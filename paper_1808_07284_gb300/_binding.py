@@ -23,7 +23,7 @@ EXPORTS = (
     "emd_dyn_solve", "emd_batched_workspace_size", "emd_dyn_solve_batched", "emd_adjoint",
     "emd_status_string", "emd_dyn_solve_noalloc", "emd_default_mg_params", "emd_mg_workspace_size",
     "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time", "emd_dyn_solve_mg",
-    "emd_dyn_solve_batched_mg", "emd_lsd",
+    "emd_dyn_solve_batched_mg", "emd_lsd", "emd_batched_adjoint_workspace_size", "emd_adjoint_batched",
 )
 
 
@@ -105,6 +105,12 @@ def lib() -> ctypes.CDLL:
         L.emd_adjoint.argtypes = [c_void_p, c_int, c_int, c_double, c_double, c_int, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
         L.emd_adjoint.restype = c_int
+        L.emd_batched_adjoint_workspace_size.argtypes = [c_int]
+        L.emd_batched_adjoint_workspace_size.restype = c_size_t
+        L.emd_adjoint_batched.argtypes = [c_int, P(c_void_p), P(c_int), P(c_int), P(c_double),
+                                          P(c_double), c_int, c_void_p, P(c_void_p), P(c_void_p),
+                                          c_void_p, c_size_t, c_void_p]
+        L.emd_adjoint_batched.restype = c_int
         L.emd_dyn_solve_noalloc.argtypes = [c_void_p, c_void_p, c_int, c_int, c_double, c_double,
                                             P(EmdParams), c_void_p, c_void_p, P(EmdResult), c_void_p]
         L.emd_dyn_solve_noalloc.restype = c_int
@@ -281,6 +287,32 @@ def emd_adjoint(phi, dt, dx, balance, grad_out, grad_pred, grad_obs, workspace, 
                            _ptr(grad_obs), _ptr(workspace), workspace.numel(), _stream(stream))
     if st != EMD_OK:
         raise EmdError(st, "emd_adjoint")
+
+
+def emd_batched_adjoint_workspace_size(B: int) -> int:
+    return lib().emd_batched_adjoint_workspace_size(B)
+
+
+def emd_adjoint_batched(phis, dts, dxs, balance, grad_out, grad_preds, grad_obss, workspace, stream=None):
+    """Adjoint sources of B gathers in two launches (Sec. 2.3); grad_out is a device vector of B
+    floats or None; grad_obss a list (entries may be None) or None."""
+    B = len(phis)
+    nts, nrs = [int(t.shape[1]) for t in phis], [int(t.shape[0]) for t in phis]
+    for b in range(B):
+        _check_grid(phis[b], nrs[b], nts[b], f"phi[{b}]")
+        _check_grid(grad_preds[b], nrs[b], nts[b], f"grad_pred[{b}]")
+        if grad_obss is not None and grad_obss[b] is not None:
+            _check_grid(grad_obss[b], nrs[b], nts[b], f"grad_obs[{b}]")
+    if grad_out is not None and (grad_out.numel() != B or not grad_out.is_contiguous()):
+        raise ValueError("grad_out must be a contiguous device vector of B floats")
+    P = c_void_p * B
+    go = None if grad_obss is None else P(*[_ptr(t) for t in grad_obss])
+    st = lib().emd_adjoint_batched(B, P(*[_ptr(t) for t in phis]), (c_int * B)(*nts), (c_int * B)(*nrs),
+                                   (c_double * B)(*dts), (c_double * B)(*dxs), balance, _ptr(grad_out),
+                                   P(*[_ptr(t) for t in grad_preds]), go, _ptr(workspace),
+                                   workspace.numel(), _stream(stream))
+    if st != EMD_OK:
+        raise EmdError(st, "emd_adjoint_batched")
 
 
 def emd_dyn_solve_noalloc(f_obs, f_pred, dt, dx, params: EmdParams, phi, m, stream=None,

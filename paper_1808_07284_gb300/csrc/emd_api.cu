@@ -270,6 +270,8 @@ struct SolveExtra {
   const float *const *phi_init = nullptr;
   const float *const *m_init = nullptr;
   bool finalize = true;
+  bool no_tune = false;   // tile 0 takes the untuned default shape (no timed trial solves)
+  bool no_graph = false;  // per-pass fallback by plain launches (capturing a graph allocates)
 };
 
 emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
@@ -370,7 +372,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   for (int b = 0; b < B; ++b) max_cells = std::max(max_cells, static_cast<long long>(nt[b]) * nr[b]);
   // Small gathers: one CTA per gather keeps the whole solve in shared memory.
   const bool resident = p.launch_mode == 0 && p.tile == 0 && max_cells <= emd::kResidentMaxCells;
-  if (p.tile == 0 && !resident && si == kTmaShape)
+  if (p.tile == 0 && !resident && si == kTmaShape && !x.no_tune)
     si = autotune_shape(B, f_obs, f_pred, nt, nr, dt, dx, p, phi, m, results, ws, ws_bytes, stream,
                         x);
   const Shape &sh = kShapes[si];
@@ -498,7 +500,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     }
     (void)cudaGetLastError();
   }
-  PassLauncher passes(sh, ctl, grid, p.launch_mode == 1 ? 1 : 2);
+  PassLauncher passes(sh, ctl, grid, p.launch_mode == 1 || x.no_graph ? 1 : 2);
   if (persistent || resident) {
     // every pass already enqueued
   } else if (p.tol <= 0.0) {
@@ -720,6 +722,23 @@ emd_status mg_impl(int B, const float *const *f_obs, const float *const *f_pred,
 
 }  // namespace
 
+namespace emd_internal {
+
+// emd_dyn_solve for the no-allocation entry point (emd_noalloc.cu): no autotuner trials
+// and no CUDA graph.  Not exported.
+__attribute__((visibility("hidden"))) emd_status solve_without_allocation(
+    const float *f_obs, const float *f_pred, int nt, int nr, double dt, double dx,
+    const emd_params *params, float *phi, float *m, emd_result *result, void *workspace,
+    size_t ws_bytes, cudaStream_t stream) {
+  SolveExtra x;
+  x.no_tune = true;
+  x.no_graph = true;
+  return solve_impl(1, &f_obs, &f_pred, &nt, &nr, &dt, &dx, params, &phi, &m, result, workspace,
+                    ws_bytes, stream, x);
+}
+
+}  // namespace emd_internal
+
 extern "C" {
 
 void emd_default_params(emd_params *p) {
@@ -822,6 +841,55 @@ emd_status emd_adjoint(const float *phi, int nt, int nr, double dt, double dx, i
   }
   emd::k_adj_scale<<<blocks, kThreads, 0, stream>>>(phi, n, area, balance, acc, grad_out,
                                                      grad_pred, grad_obs);
+  EMD_CK(cudaGetLastError());
+  return EMD_OK;
+}
+
+size_t emd_batched_adjoint_workspace_size(int B) {
+  if (B < 1) return 0;
+  return align256(sizeof(emd::AdjJob) * static_cast<size_t>(B)) + align256(sizeof(double) * B);
+}
+
+emd_status emd_adjoint_batched(int B, const float *const *phi, const int *nt, const int *nr,
+                               const double *dt, const double *dx, int balance,
+                               const float *grad_out, float *const *grad_pred,
+                               float *const *grad_obs, void *workspace, size_t ws_bytes,
+                               emd_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (B < 1 || !phi || !nt || !nr || !dt || !dx || !grad_pred) return EMD_ERR_ARG;
+  if (balance != EMD_BAL_NONE && balance != EMD_BAL_MEAN) return EMD_ERR_ARG;
+  if (B > 65535) return EMD_ERR_ARG;  // gathers ride on gridDim.y
+  std::vector<emd::AdjJob> jobs(B);
+  long long n_max = 0;
+  for (int b = 0; b < B; ++b) {
+    if (!phi[b] || !grad_pred[b] || !size_ok(nt[b], nr[b])) return EMD_ERR_ARG;
+    if (!(dt[b] > 0) || !std::isfinite(dt[b]) || !(dx[b] > 0) || !std::isfinite(dx[b]))
+      return EMD_ERR_ARG;
+    emd::AdjJob &J = jobs[b];
+    J.phi = phi[b];
+    J.gp = grad_pred[b];
+    J.go = grad_obs ? grad_obs[b] : nullptr;
+    J.grad_out = grad_out ? grad_out + b : nullptr;
+    J.n = static_cast<long long>(nt[b]) * nr[b];
+    J.area = nr[b] == 1 ? dt[b] : dx[b] * dt[b];
+    n_max = std::max(n_max, J.n);
+  }
+  const size_t need = emd_batched_adjoint_workspace_size(B);
+  if (!workspace || !aligned256(workspace) || ws_bytes < need) return EMD_ERR_WORKSPACE;
+  char *base = static_cast<char *>(workspace);
+  emd::AdjJob *djobs = reinterpret_cast<emd::AdjJob *>(base);
+  double *acc = reinterpret_cast<double *>(base + align256(sizeof(emd::AdjJob) * static_cast<size_t>(B)));
+  EMD_CK(cudaMemcpyAsync(djobs, jobs.data(), sizeof(emd::AdjJob) * B, cudaMemcpyHostToDevice, stream));
+  // about two waves of 256-thread blocks over the largest gather, at most 4 cells per thread
+  const int bx = static_cast<int>(std::max<long long>(
+      1, std::min<long long>((n_max + 4ll * kThreads - 1) / (4ll * kThreads),
+                             std::max(1, 2 * 8 * sm_count() / B))));
+  if (balance == EMD_BAL_MEAN) {
+    EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double) * B, stream));
+    emd::k_adj_sum_batched<<<dim3(bx, B), kThreads, 0, stream>>>(djobs, acc);
+    EMD_CK(cudaGetLastError());
+  }
+  emd::k_adj_scale_batched<<<dim3(bx, B), kThreads, 0, stream>>>(djobs, acc, balance);
   EMD_CK(cudaGetLastError());
   return EMD_OK;
 }

@@ -778,6 +778,57 @@ __global__ void __launch_bounds__(kThreads) k_adj_scale(const float *phi, size_t
   }
 }
 
+// One gather of a batched adjoint (device copy in the caller's workspace).
+struct AdjJob {
+  const float *phi;
+  float *gp, *go;          // d dist / d Pcal, and its negative (nullable)
+  const float *grad_out;   // device scalar or null (= 1)
+  long long n;             // cells
+  double area;             // dx dt (dt when nr == 1)
+};
+
+// Sums of phi of every gather of a batch: grid (X, B), acc[b] += sum of gather b (FP32 per
+// thread over a grid stride, FP64 above the warp).
+__global__ void __launch_bounds__(kThreads) k_adj_sum_batched(const AdjJob *jobs, double *acc) {
+  const AdjJob J = jobs[blockIdx.y];
+  float v[1] = {0.0f};
+  const long long stride = static_cast<long long>(gridDim.x) * kThreads;
+  for (long long i = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; i < J.n; i += stride)
+    v[0] += J.phi[i];
+  block_accumulate<1>(v, acc + blockIdx.y);
+}
+
+// grad_pred = g area (phi - mean), grad_obs = -grad_pred for gather blockIdx.y (Sec. 2.3),
+// four cells per thread where every pointer of the gather is 16-byte aligned.
+__global__ void __launch_bounds__(kThreads) k_adj_scale_batched(const AdjJob *jobs, const double *acc,
+                                                                int balance) {
+  const AdjJob J = jobs[blockIdx.y];
+  const float mean = balance ? static_cast<float>(acc[blockIdx.y] / static_cast<double>(J.n)) : 0.0f;
+  const float g = static_cast<float>((J.grad_out ? static_cast<double>(*J.grad_out) : 1.0) * J.area);
+  const long long stride = static_cast<long long>(gridDim.x) * kThreads;
+  const long long t0 = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(J.phi) | reinterpret_cast<uintptr_t>(J.gp) |
+                     reinterpret_cast<uintptr_t>(J.go)) & 15u) == 0;
+  long long done = 0;
+  if (vec) {
+    const long long n4 = J.n / 4;
+    const float4 *p4 = reinterpret_cast<const float4 *>(J.phi);
+    float4 *gp4 = reinterpret_cast<float4 *>(J.gp), *go4 = reinterpret_cast<float4 *>(J.go);
+    for (long long i = t0; i < n4; i += stride) {
+      const float4 x = p4[i];
+      const float4 y = make_float4(g * (x.x - mean), g * (x.y - mean), g * (x.z - mean), g * (x.w - mean));
+      gp4[i] = y;
+      if (go4) go4[i] = make_float4(-y.x, -y.y, -y.z, -y.w);
+    }
+    done = 4 * n4;
+  }
+  for (long long i = done + t0; i < J.n; i += stride) {
+    const float y = g * (J.phi[i] - mean);
+    J.gp[i] = y;
+    if (J.go) J.go[i] = -y;
+  }
+}
+
 // ------------------------------------------------------------------------------ decompose
 
 // mu = Pcal+ + Pobs-, nu = Pobs+ + Pcal- (Sec. 2.1) and their FP64 sums.

@@ -1,11 +1,12 @@
 // emd_dyn_solve_noalloc: one EMD solve with no device allocation by anyone.
 //
-// Some callers cannot call cudaMalloc: code running while a stream is being captured
-// into a CUDA graph (an allocation there is an error or breaks the capture), code under
-// a host framework whose allocator owns all device memory, or a real-time loop that must
-// never block on the allocator.  This entry point serves them.  Its scratch space is a
-// file-scope device array compiled into the library, so every GPU that loads the library
-// holds kScratchBytes of it until the process exits.
+// Some callers cannot call cudaMalloc: code whose host framework owns every device
+// allocation (a custom allocator, a fixed memory budget), a real-time loop that must never
+// block on the allocator, or a plug-in handed only its input and output buffers.  This
+// entry point serves them.  Its scratch space is a file-scope device array compiled into
+// the library, so every GPU that loads the library holds kScratchBytes of it until the
+// process exits.  The solve itself takes no step that allocates behind the caller's back:
+// no autotuner trial solves and no CUDA graph (see solve_without_allocation).
 //
 // The array's name in host code is only a host-side stand-in: passing it to a kernel
 // would fault (or, where the GPU can reach host memory, silently use the wrong memory).
@@ -16,6 +17,13 @@
 #include <mutex>
 
 #include "emd_gb300.h"
+
+namespace emd_internal {
+emd_status solve_without_allocation(const float *f_obs, const float *f_pred, int nt, int nr,
+                                    double dt, double dx, const emd_params *params, float *phi,
+                                    float *m, emd_result *result, void *workspace,
+                                    size_t ws_bytes, cudaStream_t stream);
+}
 
 namespace {
 
@@ -59,13 +67,13 @@ extern "C" emd_status emd_dyn_solve_noalloc(const float *f_obs, const float *f_p
   emd_params p;
   emd_default_params(&p);
   if (params) p = *params;
-  // Plain launches only: instantiating a CUDA graph would allocate.
-  p.launch_mode = 1;
+  if (p.launch_mode == 2) p.launch_mode = 1;  // graph replays would instantiate a graph
   void *ws = nullptr;
   const emd_status s = scratch_address(&ws);
   if (s != EMD_OK) return s;
   // The solve clears everything that must start at zero (state, accumulators, counters)
   // and rewrites every plane it reads, so the previous call's contents do not matter.
-  return emd_dyn_solve(f_obs, f_pred, nt, nr, dt, dx, &p, phi, m, result, ws, kScratchBytes,
-                       stream);
+  return emd_internal::solve_without_allocation(f_obs, f_pred, nt, nr, dt, dx, &p, phi, m, result,
+                                                ws, kScratchBytes,
+                                                reinterpret_cast<cudaStream_t>(stream));
 }

@@ -1,10 +1,11 @@
 """The no-allocation solve entry point against the regular one (needs a GPU).
 
-emd_dyn_solve_noalloc serves callers that cannot allocate device memory (code inside a
-stream capture, code whose framework owns the allocator); it runs on a scratch array
-built into the library.  Two calls in a row must each give the regular entry point's
-result, within the parity tolerances of the other GPU tests.  This file sorts last so
-that a run stopping at the first failure has run every other test before it.
+emd_dyn_solve_noalloc serves callers that cannot allocate device memory (code whose host
+framework owns every device allocation, loops that must not block on an allocation); it
+runs on a scratch array built into the library.  Two calls in a row must each give the
+regular entry point's result, within the parity tolerances of the other GPU tests.  This
+file sorts last so that a run stopping at the first failure has run every other test
+before it.
 """
 
 import numpy as np
