@@ -72,6 +72,7 @@ def _args():
                     default=None, help="run --warmup solves of a named case (for ncu) and exit")
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--shots", type=int, default=8, help="--profile marine-batch: number of shots")
+    ap.add_argument("--tile", type=int, default=PROFILE_TILE, help="--profile: tile-shape id to run")
     ap.add_argument("--workload", choices=["marine128", "transmissive", "uneven48", "uneven48-residual"],
                     default="marine128")
     return ap.parse_args()
@@ -122,11 +123,21 @@ def _kernel_hash():
     """Hash of the device code of the fused pass, comments and whitespace removed: a
     traffic capture stays valid across edits of comments only."""
     h = hashlib.sha256()
-    for rel in ("paper_1808_07284_gb300/csrc/emd_kernels.cuh", "paper_1808_07284_gb300/csrc/emd_pass_tma.cuh"):
+    for rel in ("paper_1808_07284_gb300/csrc/emd_kernels.cuh", "paper_1808_07284_gb300/csrc/emd_pass_tma.cuh",
+                "paper_1808_07284_gb300/csrc/emd_march.cuh"):
         with open(os.path.join(ROOT, rel)) as fh:
             code = re.sub(r"//[^\n]*", "", fh.read())
         h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
+
+
+def _kernel_of(tile):
+    """Name of the persistent pass kernel a tile-shape id runs (see include/emd_gb300.h)."""
+    if tile >= 10:
+        return "k_solve_march", {10: "<11, 6, 1>", 11: "<11, 4, 1>"}.get(tile, "")
+    if tile >= 7:
+        return "k_solve_tma", {7: "<13, 2, 8, 2>", 8: "<8, 3, 8, 2>", 9: "<21, 1, 8, 2>"}[tile]
+    return "k_pass", ""
 
 
 def _traffic(name, cells):
@@ -392,7 +403,8 @@ def run_marine(a):
     t_pass = (timed_solve(n2) - timed_solve(n1)) / (n2 - n1)
     peak, peak_kind = _peaks()
     achieved = CELL_BYTES * cells / t_pass / 1e9
-    traffic = _traffic("k_solve_tma_traffic_marine.json", cells)
+    kname, kargs = _kernel_of(res[0].tile)
+    traffic = _traffic(f"{kname}_traffic_marine.json", cells)
 
     # ---- end to end through the public API: pinned host gathers in, adjoint sources out
     h_obs = [torch.from_numpy(o).pin_memory() for o, _ in pairs]
@@ -480,7 +492,8 @@ def run_marine(a):
             "hbm_gbs_algorithmic": achieved,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_solve_tma (one fused PDHG iteration per pass of a persistent launch)",
+                         "kernel": f"{kname}{kargs} (tile id {res[0].tile}, the autotuner's choice; one fused "
+                                   "PDHG iteration per pass of a persistent launch)",
                          "note": f"{CELL_BYTES} B/cell x {cells} cells per pass over the live per-pass "
                                  f"duration {t_pass * 1e6:.1f} us (difference of {n2}- and {n1}-iteration "
                                  f"batched solves); peak {peak_kind} copy bandwidth"},
@@ -607,7 +620,7 @@ def run_profile(a):
         O_ = [torch.from_numpy(o).to(dev) for o, _ in pairs]
         P_ = [torch.from_numpy(p).to(dev) for _, p in pairs]
         for _ in range(max(1, a.warmup)):
-            d, _, _, infos = P.emd_batched(O_, P_, M_DT, M_DX, max_iter=a.iters, tile=PROFILE_TILE)
+            d, _, _, infos = P.emd_batched(O_, P_, M_DT, M_DX, max_iter=a.iters, tile=a.tile)
         torch.cuda.synchronize()
         print(json.dumps({"profile": a.profile, "shots": a.shots, "iters": infos[0]["iters"],
                           "cells": a.shots * M_NT * M_NR, "status": [i["status"] for i in infos][:4]}))
@@ -627,7 +640,7 @@ def run_profile(a):
         else:
             # the tile shape the benchmark's autotuner settles on, fixed: under a profiler
             # the autotuner's trial timings are distorted and it may pick another shape
-            d, phi, m, info = P.emd(o, p, dt, dx, max_iter=a.iters, tile=PROFILE_TILE)
+            d, phi, m, info = P.emd(o, p, dt, dx, max_iter=a.iters, tile=a.tile)
     torch.cuda.synchronize()
     print(json.dumps({"profile": a.profile, "shape": list(obs.shape), "iters": info["iters"],
                       "dist": d, "status": info["status"]}))

@@ -131,12 +131,17 @@ typedef struct {
   int ls_trials;      /* linesearch trials in total (>= iters)                           */
   int status;         /* emd_status of this solve                                        */
   int launches;       /* kernel launches this solve made (a graph's nodes count one each) */
+  int tile;           /* tile-shape id the solve ran (1..emd_tile_count(); the autotuner's
+                         choice when params->tile was 0); 0 for the shared-memory solve     */
 } emd_result;
 
 /* Fills *p with the defaults listed above.  p must not be NULL. */
 void emd_default_params(emd_params *p);
 
-/* Number of stencil tile shapes compiled into the library (valid ids: 1..count). */
+/* Number of stencil tile shapes compiled into the library (valid ids: 1..count).  Ids 1-6
+ * are the plain-staging pass (16/8/32 x 120, 8/16 x 248, 1 x 248 tiles), 7-9 the
+ * TMA-staged tile pass (13, 8 and 21 x 120 tiles), 10-11 the marching pass (a warp walks
+ * 120-sample strips down the receivers with 6 or 4 rows in flight). */
 int emd_tile_count(void);
 
 /* Bytes of device workspace emd_dyn_solve needs for one nr x nt gather (0 if invalid). */

@@ -58,6 +58,7 @@ class EmdResult(ctypes.Structure):
         ("imbalance", c_double), ("residual", c_double), ("r_feas", c_double), ("r_step", c_double),
         ("duality_gap", c_double), ("alpha", c_double), ("theta", c_double),
         ("iters", c_int), ("ls_trials", c_int), ("status", c_int), ("launches", c_int),
+        ("tile", c_int),
     ]
 
     def as_dict(self) -> dict:

@@ -14,6 +14,7 @@
 #include "emd_gb300.h"
 #include "emd_kernels.cuh"
 #include "emd_lsd.cuh"
+#include "emd_march.cuh"
 #include "emd_multigrid.cuh"
 #include "emd_pass_tma.cuh"
 #include "emd_resident.cuh"
@@ -36,23 +37,36 @@ using emd::State;
 
 // Stencil tile shapes (TI rows x (W - 8) time samples per tile); id = index + 1.
 // `iter_tma` marks the persistent TMA-staged pass (its finalize pass is the plain one
-// with the same tiling).
+// with the same tiling).  `solve_march` marks the marching persistent solve (emd_march.cuh:
+// NW marching warps per CTA, a ring of D staged rows per warp); its finalize pass, and its
+// per-pass fallback where no cooperative launch is possible, are the plain pass with
+// TI x (W - 8) tiles.
 struct Shape {
   int ti, w;
   void (*iter)(Ctl);
   void (*fin)(Ctl);
   void (*iter_tma)(Ctl, int);
-  void (*solve_tma)(Ctl, int, int);  // every pass in one cooperative launch
-  int minb;                           // TMA pass: CTAs per SM it is compiled for
+  void (*solve_tma)(Ctl, int, int, int);  // passes [k_begin, k_end) in one cooperative launch
+  int minb;                           // persistent pass: CTAs per SM it is compiled for
   int nw, ns;                         // persistent solve: compute warps, shared-memory stages
+                                      // (marching solve: rows in flight per warp)
+  void (*solve_march)(Ctl, int, int, int);  // passes [k_begin, k_end), marching warps
 };
 
-#define EMD_SHAPE(TI, W) \
-  Shape { TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr, nullptr, 0, 0, 0 }
+#define EMD_SHAPE(TI, W)                                                                      \
+  Shape {                                                                                     \
+    TI, W, emd::k_pass<TI, W, false>, emd::k_pass<TI, W, true>, nullptr, nullptr, 0, 0, 0,    \
+        nullptr                                                                               \
+  }
 #define EMD_TMA_SHAPE(TI, MINB, NW, NS)                                                     \
   Shape {                                                                                   \
     TI, 128, nullptr, emd::k_pass<TI, 128, true>, emd::k_pass_tma<TI, MINB>,                \
-        emd::k_solve_tma<TI, MINB, NW, NS>, MINB, NW, NS                                    \
+        emd::k_solve_tma<TI, MINB, NW, NS>, MINB, NW, NS, nullptr                           \
+  }
+#define EMD_MARCH_SHAPE(NW, D, MINB)                                                        \
+  Shape {                                                                                   \
+    16, 128, emd::k_pass<16, 128, false>, emd::k_pass<16, 128, true>, nullptr, nullptr, MINB, \
+        NW, D, emd::k_solve_march<NW, D, MINB>                                              \
   }
 // (A 13 x 120 shape with one CTA per SM, sixteen compute warps and four stages -- three
 // tiles in flight -- passed the parity tests but was 20-45 % slower on gathers larger
@@ -61,12 +75,17 @@ const Shape kShapes[] = {EMD_SHAPE(16, 128),          EMD_SHAPE(8, 128),
                          EMD_SHAPE(32, 128),          EMD_SHAPE(8, 256),
                          EMD_SHAPE(16, 256),          EMD_SHAPE(1, 256),
                          EMD_TMA_SHAPE(13, 2, 8, 2),  EMD_TMA_SHAPE(8, 3, 8, 2),
-                         EMD_TMA_SHAPE(21, 1, 8, 2)};
+                         EMD_TMA_SHAPE(21, 1, 8, 2),  EMD_MARCH_SHAPE(11, 6, 1),
+                         EMD_MARCH_SHAPE(11, 4, 1)};
+// (Marching solves need about 165 registers a thread; a scheduler's 16,384 registers then
+// hold three warps, so a CTA of eleven marching warps and the decider fills an SM.  Fifteen
+// marching warps at 128 registers spill inside the row loop and ran 1.65 times slower.)
 #undef EMD_SHAPE
 #undef EMD_TMA_SHAPE
+#undef EMD_MARCH_SHAPE
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kTmaShape = 6;         // 13 x 120, two CTAs per SM: the untuned default
-constexpr int kTmaFirst = 6, kTmaLast = 8;
+constexpr int kTmaFirst = 6;         // shapes kTmaFirst .. kNumShapes - 1 run persistent solves
 
 // Dynamic shared memory of the plain pass / finalize pass of a shape, of its per-pass
 // TMA kernel (two stages of six (TI + 4) x 128 planes, plus alignment slack) and of its
@@ -76,8 +95,11 @@ size_t iter_smem_bytes(const Shape &s) {
   return s.iter_tma ? 2u * 6u * (s.ti + 4) * 128u * sizeof(float) + 128u : smem_bytes(s);
 }
 size_t solve_smem_bytes(const Shape &s) {
+  if (s.solve_march)  // per warp: the ring of ns rows of six planes and three scratch rows
+    return static_cast<size_t>(s.nw) * (6u * s.ns + 3u) * emd::kMarchW * sizeof(float) + 128u;
   return static_cast<size_t>(s.ns) * 6u * (s.ti + 4) * 128u * sizeof(float) + 128u;
 }
+bool uses_tma(const Shape &s) { return s.iter_tma != nullptr; }
 
 // cuTensorMapEncodeTiled, reached through the runtime (no link against libcuda).
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -124,7 +146,7 @@ bool size_ok(int nt, int nr) {
 // Workspace: [states | shots | accumulators | tile_shot | n_done + scratch] then, per gather, the
 // pitched planes f, u0 (x,t), u1 (x,t), u2 (x,t), phi0, phi1 (36 bytes per cell).
 struct Layout {
-  size_t states, shots, acc, tiles, misc, header, total;
+  size_t states, shots, acc, tiles, units, misc, header, total;
   std::vector<size_t> gather;  // offset of each gather's planes
   std::vector<size_t> plane;   // bytes of one plane (256-aligned)
   int max_tiles;
@@ -142,7 +164,12 @@ Layout layout(int B, const int *nt, const int *nr) {
   L.shots = align256(sizeof(State) * B);
   L.acc = L.shots + align256(sizeof(Shot) * B);
   L.tiles = L.acc + align256(sizeof(double) * emd::kAccBufs * emd::kSpread * emd::kAcc * B);
-  L.misc = L.tiles + align256(sizeof(int) * static_cast<size_t>(L.max_tiles));
+  size_t max_units = 0;  // marching units: 120-sample strips x segments of >= kMarchMinSeg rows
+  for (int b = 0; b < B; ++b)
+    max_units += static_cast<size_t>((nt[b] + emd::kMarchTJ - 1) / emd::kMarchTJ) *
+                 ((nr[b] + emd::kMarchMinSeg - 1) / emd::kMarchMinSeg);
+  L.units = L.tiles + align256(sizeof(int) * static_cast<size_t>(L.max_tiles));
+  L.misc = L.units + align256(sizeof(int) * max_units);
   L.header = L.misc + 256;
   size_t off = L.header;
   for (int b = 0; b < B; ++b) {
@@ -153,6 +180,33 @@ Layout layout(int B, const int *nt, const int *nr) {
   }
   L.total = off;
   return L;
+}
+
+// Segments of the marching solve for T marching warps.  When the batch holds at most 64
+// strip-rows per warp, segments are sized so that no warp gets more than one unit (a pass
+// then costs one unit per warp, and a second unit would double it); larger batches get about
+// 16 units per warp, so that whole units leave the warps within about 1/16 of one another.
+// Segments are never shorter than kMarchMinSeg receivers (each carries a 4-row halo).  Fills
+// the gathers' unit fields and the unit -> gather list.
+void march_units(std::vector<Shot> &shots, std::vector<int> &unit_shot, long long T) {
+  long long R = 0;  // strip-rows of the batch
+  for (const Shot &S : shots)
+    R += static_cast<long long>((S.nt + emd::kMarchTJ - 1) / emd::kMarchTJ) * S.nr;
+  T = std::max(1ll, T);
+  const bool one_each = R <= 64 * T;
+  const long long H = std::max<long long>(emd::kMarchMinSeg, one_each ? (R + T - 1) / T : R / (16 * T));
+  unit_shot.clear();
+  for (size_t b = 0; b < shots.size(); ++b) {
+    Shot &S = shots[b];
+    S.strips = (S.nt + emd::kMarchTJ - 1) / emd::kMarchTJ;
+    long long nseg = one_each ? S.nr / H : (S.nr + H - 1) / H;
+    nseg = std::max(1ll, std::min<long long>(nseg, (S.nr + emd::kMarchMinSeg - 1) / emd::kMarchMinSeg));
+    S.seg_h = static_cast<int>((S.nr + nseg - 1) / nseg);
+    nseg = (S.nr + S.seg_h - 1) / S.seg_h;
+    S.unit0 = static_cast<int>(unit_shot.size());
+    S.nunits = static_cast<int>(S.strips * nseg);
+    unit_shot.insert(unit_shot.end(), S.nunits, static_cast<int>(b));
+  }
 }
 
 bool params_ok(const emd_params &p) {
@@ -187,6 +241,9 @@ bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255u) 
 
 // With tol > 0 the host checks the finished-gather count after every kPoll passes.
 constexpr int kPoll = 64;
+// A batched persistent solve with tol > 0 is re-dealt over the CTAs every kRebalance
+// stopping tests (check_every passes each).
+constexpr int kRebalance = 16;
 
 // Enqueues fused passes on a stream: replays of one CUDA graph of kChunk passes,
 // captured once per solve, plus plain launches for the remainder (launch_mode 1: plain
@@ -329,7 +386,7 @@ int autotune_shape(int B, const float *const *f_obs, const float *const *f_pred,
   };
   int best = kTmaShape;
   float best_t = 0.0f;
-  for (int shape = kTmaFirst; shape <= kTmaLast; ++shape) {
+  for (int shape = kTmaFirst; shape < kNumShapes; ++shape) {
     (void)timed(shape, 4);  // first use: module load, attribute set-up
     const float t1 = timed(shape, 8), t2 = timed(shape, 40);
     if (t1 < 0.0f || t2 < 0.0f) continue;
@@ -367,7 +424,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   if (!ws || !aligned256(ws) || ws_bytes < L.total) return EMD_ERR_WORKSPACE;
 
   int si = pick_shape(p, B, nt, nr);
-  if (kShapes[si].iter_tma && !encode_fn()) si = 0;  // no TMA descriptors: plain staging
+  if (uses_tma(kShapes[si]) && !encode_fn()) si = 0;  // no TMA descriptors: plain staging
   long long max_cells = 0;
   for (int b = 0; b < B; ++b) max_cells = std::max(max_cells, static_cast<long long>(nt[b]) * nr[b]);
   // Small gathers: one CTA per gather keeps the whole solve in shared memory.
@@ -402,7 +459,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     }
     S.ph[0] = reinterpret_cast<float *>(g + 7 * pl);
     S.ph[1] = reinterpret_cast<float *>(g + 8 * pl);
-    if (sh.iter_tma && !encode_tmap(S, g, pl, sh.ti + 4)) return EMD_ERR_CUDA;
+    if (uses_tma(sh) && !encode_tmap(S, g, pl, sh.ti + 4)) return EMD_ERR_CUDA;
     S.tiles_j = (nt[b] + (sh.w - 8) - 1) / (sh.w - 8);
     S.tile0 = static_cast<int>(tile_shot.size());
     S.ntiles = tiles_of(sh, nt[b], nr[b]);
@@ -415,10 +472,14 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     nr_max = std::max(nr_max, nr[b]);
   }
   const int grid = static_cast<int>(tile_shot.size());
+  std::vector<int> unit_shot;  // marching solve: its unit list
+  if (sh.solve_march)
+    march_units(shots, unit_shot, static_cast<long long>(sh.nw) * sh.minb * sm_count());
 
   State *states = reinterpret_cast<State *>(base + L.states);
   Shot *dshots = reinterpret_cast<Shot *>(base + L.shots);
   int *dtiles = reinterpret_cast<int *>(base + L.tiles);
+  int *dunits = reinterpret_cast<int *>(base + L.units);
   int *n_done = reinterpret_cast<int *>(base + L.misc);
   int *err_flag = n_done + 1;
   double *acc = reinterpret_cast<double *>(base + L.acc);
@@ -426,6 +487,9 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   EMD_CK(cudaMemcpyAsync(dshots, shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
   EMD_CK(cudaMemcpyAsync(dtiles, tile_shot.data(), sizeof(int) * tile_shot.size(),
                          cudaMemcpyHostToDevice, stream));
+  if (!unit_shot.empty())
+    EMD_CK(cudaMemcpyAsync(dunits, unit_shot.data(), sizeof(int) * unit_shot.size(),
+                           cudaMemcpyHostToDevice, stream));
   EMD_CK(cudaMemsetAsync(states, 0, sizeof(State) * B, stream));
   EMD_CK(cudaMemsetAsync(n_done, 0, 2 * sizeof(int), stream));
   EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double) * emd::kAccBufs * emd::kSpread * emd::kAcc * B,
@@ -449,6 +513,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   ctl.states = states;
   ctl.acc = acc;
   ctl.tile_shot = dtiles;
+  ctl.unit_shot = dunits;
   ctl.n_done = n_done;
   ctl.error = err_flag;
   ctl.trace = p.trace;
@@ -477,26 +542,73 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   }
   // One cooperative launch for the whole solve, when the TMA pass is in use and every CTA
   // of the grid can be resident at once (its CTAs wait on one another between passes).
+  // A batch solved to a tolerance runs in chunks of kRebalance checks instead: after each
+  // chunk the host drops the gathers that have stopped and deals the tiles of the running
+  // ones over every CTA again, so CTAs do not idle while the slowest gathers go on (the
+  // per-gather counters are cumulative, so a chunk resumes where the last one stopped).
   bool persistent = false;
-  if (!resident && p.launch_mode == 0 && sh.solve_tma) {
+  if (!resident && p.launch_mode == 0 && (sh.solve_tma || sh.solve_march)) {
+    const bool march = sh.solve_march != nullptr;
+    void (*fn)(Ctl, int, int, int) = march ? sh.solve_march : sh.solve_tma;
+    const std::vector<int> &work = march ? unit_shot : tile_shot;  // every gather's work items
+    int *dwork = march ? dunits : dtiles;
     int dev = 0, coop = 0, per_sm = 0;
     const size_t tsmem = solve_smem_bytes(sh);
-    const int tthreads = (sh.nw + 2) * 32;
+    const int tthreads = (sh.nw + (march ? 1 : 2)) * 32;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
-        cudaFuncSetAttribute(sh.solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(tsmem)) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sh.solve_tma, tthreads, tsmem) ==
-            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tthreads, tsmem) == cudaSuccess &&
         per_sm >= 1) {
-      int tiles = grid, passes = p.max_iter;
-      const int cgrid = std::min(tiles, std::min(per_sm, sh.minb) * sm_count());
-      Ctl cctl = ctl;
-      void *args[] = {&cctl, &tiles, &passes};
-      EMD_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(sh.solve_tma), dim3(cgrid),
-                                         dim3(tthreads), args, tsmem, stream));
-      persistent = true;
-      n_launch += 1;
+      const long long chunk =
+          p.tol > 0.0 && B > 1 ? static_cast<long long>(kRebalance) * p.check_every : p.max_iter;
+      const int cap = std::min(per_sm, sh.minb) * sm_count();  // co-resident CTAs
+      std::vector<int> run;  // the chunk's work list (empty: the full list)
+      std::vector<Shot> run_shots;
+      long long k0 = 0;
+      while (k0 < p.max_iter) {
+        const int kb = static_cast<int>(k0);
+        const int ke = static_cast<int>(std::min<long long>(p.max_iter, k0 + chunk));
+        int items = static_cast<int>(run.empty() ? work.size() : run.size()), kb_ = kb, ke_ = ke;
+        const int cgrid = march ? std::min((items + sh.nw - 1) / sh.nw, cap) : std::min(items, cap);
+        Ctl cctl = ctl;
+        void *args[] = {&cctl, &items, &kb_, &ke_};
+        EMD_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(fn), dim3(cgrid), dim3(tthreads),
+                                           args, tsmem, stream));
+        persistent = true;
+        n_launch += 1;
+        k0 = ke;
+        if (k0 >= p.max_iter) break;
+        // which gathers are still running (and did a bounded wait give up)?
+        std::vector<State> hs(B);
+        int h_flags[2] = {0, 0};
+        EMD_CK(cudaMemcpyAsync(hs.data(), states, sizeof(State) * B, cudaMemcpyDeviceToHost, stream));
+        EMD_CK(cudaMemcpyAsync(h_flags, n_done, sizeof(h_flags), cudaMemcpyDeviceToHost, stream));
+        EMD_CK(cudaStreamSynchronize(stream));
+        if (h_flags[1] || h_flags[0] >= B) break;
+        std::vector<int> next;
+        run_shots = shots;
+        for (int b = 0; b < B; ++b) {
+          if (hs[b].done) continue;
+          Shot &S = run_shots[b];
+          (march ? S.unit0 : S.tile0) = static_cast<int>(next.size());
+          next.insert(next.end(), march ? S.nunits : S.ntiles, b);
+        }
+        const size_t now = run.empty() ? work.size() : run.size();
+        if (next.size() != now) {  // some gathers stopped: deal the rest over every CTA
+          run.swap(next);
+          EMD_CK(cudaMemcpyAsync(dshots, run_shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice,
+                                 stream));
+          EMD_CK(cudaMemcpyAsync(dwork, run.data(), sizeof(int) * run.size(), cudaMemcpyHostToDevice,
+                                 stream));
+        }
+      }
+      if (!run.empty()) {  // the finalize pass walks every gather's tiles
+        EMD_CK(cudaMemcpyAsync(dshots, shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
+        EMD_CK(cudaMemcpyAsync(dwork, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice,
+                               stream));
+      }
     }
     (void)cudaGetLastError();
   }
@@ -560,6 +672,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     r.ls_trials = st.trials;
     r.status = st.status;
     r.launches = n_launch;
+    r.tile = resident ? 0 : si + 1;
     if (first == EMD_OK && st.status != EMD_OK) first = static_cast<emd_status>(st.status);
   }
   return first;

@@ -48,6 +48,8 @@ struct Shot {
   float *ph[2];                     // phi^m lives in ph[m & 1], pitched
   int nt, nr, ntp, tiles_j;         // ntp: row pitch in floats (multiple of 32)
   int tile0, ntiles;                // first global tile index and tile count of this gather
+  int unit0, nunits;                // marching pass: first global unit index and unit count
+  int strips, seg_h;                // marching pass: 120-sample strips, receivers per segment
   float rdx, rdt;                   // 1/dx (0 when nr == 1), 1/dt
   double area, lambda;              // dx*dt (dt when nr == 1); 4/dx^2 + 4/dt^2
 };
@@ -83,6 +85,7 @@ struct Ctl {
   State *states;
   double *acc;                      // [gather][kAccBufs][kSpread][kAcc] FP64 accumulators (zeroed)
   const int *tile_shot;             // global tile -> gather
+  const int *unit_shot;             // marching pass: global unit -> gather
   int *n_done;                      // gathers finished
   int *error;                       // set to 1 when a bounded device wait gives up
   double *trace;                    // optional [gather][max_iter][4] history (or null)

@@ -691,11 +691,59 @@ __device__ __forceinline__ void warp_totals(const double *acc, double (&out)[9])
   for (int m = 0; m < 9; ++m) out[m] = __shfl_sync(FULL, c[0], 2 * m);
 }
 
+// Decider warp of a persistent solve: decisions k_begin .. k_end - 1 of the gathers g_lo ..
+// g_hi for which owns(S) holds.  Decision k of a gather waits until its cumulative count of
+// finished work units reaches (k + 1) count(S), sums the pass's accumulators, decides,
+// publishes the new state and releases epoch = k + 1.  The state load and the FP64
+// preparation overlap the pass; the warp is the only writer of the gather's state.
+template <class Owns, class Count>
+__device__ __forceinline__ void decider_loop(const Ctl &c, int g_lo, int g_hi, int k_begin,
+                                             int k_end, Owns owns, Count count) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  if (c.debug_fault == 2) return;  // test hook: no decision is ever published
+  for (int k = k_begin; k < k_end; ++k) {
+    bool any = false;
+    for (int g = g_lo; g <= g_hi; ++g) {
+      const Shot &S = c.shots[g];
+      if (!owns(S)) continue;
+      State *st = c.states + g;
+      if (st->done) continue;
+      any = true;
+      const DecidePrep pr = decide_prep(c, st);  // overlaps pass k's compute
+      int trials = st->trials;
+      // every lane waits (a wait run by one lane slows the warp's later shuffles)
+      const bool ok = __all_sync(
+          FULL, wait_count(&st->tiles_done, static_cast<unsigned>(k + 1) * static_cast<unsigned>(count(S))));
+      if (!ok) {
+        if (lane == 0) atomicExch(c.error, 1);
+        return;
+      }
+      double a_[9];
+      double *acc = acc_of(c, g, k & 1);
+      warp_totals(acc, a_);
+      const Decision o = decide_publish(c, st, pr, a_, g, trials);
+      __syncwarp();  // the new state, before the release
+      if (lane == 0) {
+        st_release(&st->epoch, static_cast<unsigned>(k + 1));
+        if (o.checked) residuals(pr, a_, st->r_feas, st->r_step);
+      }
+      // pass k + 2 adds into this set again; the release of epoch k + 2 (after decision
+      // k + 1) orders these zeros before any of its flushes
+#pragma unroll
+      for (int q = lane; q < kSpread * kAcc; q += 32) acc[q] = 0.0;
+    }
+    if (!any) return;
+  }
+}
+
 // NW compute warps, one producer and one decider warp; NS shared-memory stages (the
-// producer keeps up to NS - 1 tiles loading while one is computed).
+// producer keeps up to NS - 1 tiles loading while one is computed).  Runs passes
+// [k_begin, k_end) of every gather in the tile list (a batch solved to a tolerance is run
+// in chunks, and each chunk's list holds only the gathers still running).
 template <int TI, int MINB = 2, int NW = kThreads / 32, int NS = 2>
 __global__ void __launch_bounds__((NW + 2) * 32, MINB)
-    k_solve_tma(Ctl c, int total_tiles, int max_passes) {
+    k_solve_tma(Ctl c, int total_tiles, int k_begin, int k_end) {
   using T = TmaTile<TI>;
   constexpr int NT = NW * 32;  // compute threads
   extern __shared__ float4 dyn4[];
@@ -722,49 +770,19 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB)
   __syncthreads();
 
   if (warp == NW + 1) {  // ---- decider warp: decisions of the gathers this CTA owns
-    constexpr unsigned FULL = 0xffffffffu;
-    if (c.debug_fault == 2) return;  // test hook: no decision is ever published
-    const int g_lo = c.tile_shot[t_lo], g_hi = c.tile_shot[t_hi - 1];
-    for (int k = 0; k < max_passes; ++k) {
-      bool any = false;
-      for (int g = g_lo; g <= g_hi; ++g) {
-        const Shot &S = c.shots[g];
-        if (tile_owner(S.tile0, total_tiles, gridDim.x) != static_cast<int>(blockIdx.x)) continue;
-        State *st = c.states + g;
-        if (st->done) continue;  // this warp is the only writer of the gather's state
-        any = true;
-        const DecidePrep pr = decide_prep(c, st);  // overlaps pass k's compute
-        int trials = st->trials;
-        // every lane waits (see the compute warps' pass boundary)
-        const bool ok = __all_sync(
-            FULL, wait_count(&st->tiles_done, static_cast<unsigned>(k + 1) * static_cast<unsigned>(S.ntiles)));
-        if (!ok) {
-          if (lane == 0) atomicExch(c.error, 1);
-          return;
-        }
-        double a_[9];
-        double *acc = acc_of(c, g, k & 1);
-        warp_totals(acc, a_);
-        const Decision o = decide_publish(c, st, pr, a_, g, trials);
-        __syncwarp();  // the new state, before the release
-        if (lane == 0) {
-          st_release(&st->epoch, static_cast<unsigned>(k + 1));
-          if (o.checked) residuals(pr, a_, st->r_feas, st->r_step);
-        }
-        // pass k + 2 adds into this set again; the release of epoch k + 2 (after decision
-        // k + 1) orders these zeros before any of its flushes
-#pragma unroll
-        for (int q = lane; q < kSpread * kAcc; q += 32) acc[q] = 0.0;
-      }
-      if (!any) return;
-    }
+    decider_loop(
+        c, c.tile_shot[t_lo], c.tile_shot[t_hi - 1], k_begin, k_end,
+        [&](const Shot &S) {
+          return tile_owner(S.tile0, total_tiles, gridDim.x) == static_cast<int>(blockIdx.x);
+        },
+        [](const Shot &S) { return S.ntiles; });
     return;
   }
 
   if (warp == NW) {  // ---- producer warp: one lane stages every tile of every pass
     if (lane == 0) {
       int i = 0;
-      for (int k = 0; k < max_passes; ++k) {
+      for (int k = k_begin; k < k_end; ++k) {
         bool first = true;
         for (int t = t_lo; t < t_hi; ++t, ++i) {
           const int s = i % NS;
@@ -785,7 +803,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB)
           stage_tile<TI>(c, t, sbase + s * T::STAGE, &full[s], info[s], k);
           if (first) {
             first = false;
-            if (!mbar_wait(&gob, k & 1)) {
+            if (!mbar_wait(&gob, (k - k_begin) & 1)) {
               atomicExch(c.error, 1);
               return;
             }
@@ -800,7 +818,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, MINB)
   // ---- compute warps
   float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int i = 0;
-  for (int k = 0; k < max_passes; ++k) {
+  for (int k = k_begin; k < k_end; ++k) {
     // pass boundary: is any gather of this CTA still running after decision k - 1?  The
     // whole of warp 0 waits (the same loads in every lane): a wait loop run by one lane
     // leaves the warp split, and every later shuffle of it then costs ~10x.
