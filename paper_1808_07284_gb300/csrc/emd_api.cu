@@ -86,6 +86,7 @@ const Shape kShapes[] = {EMD_SHAPE(16, 128),          EMD_SHAPE(8, 128),
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kTmaShape = 6;         // 13 x 120, two CTAs per SM: the untuned default
 constexpr int kTmaFirst = 6;         // shapes kTmaFirst .. kNumShapes - 1 run persistent solves
+constexpr int kMaxMarchWarps = 16384;  // most marching warps a launch may hold (partition table)
 
 // Dynamic shared memory of the plain pass / finalize pass of a shape, of its per-pass
 // TMA kernel (two stages of six (TI + 4) x 128 planes, plus alignment slack) and of its
@@ -164,12 +165,9 @@ Layout layout(int B, const int *nt, const int *nr) {
   L.shots = align256(sizeof(State) * B);
   L.acc = L.shots + align256(sizeof(Shot) * B);
   L.tiles = L.acc + align256(sizeof(double) * emd::kAccBufs * emd::kSpread * emd::kAcc * B);
-  size_t max_units = 0;  // marching units: 120-sample strips x segments of >= kMarchMinSeg rows
-  for (int b = 0; b < B; ++b)
-    max_units += static_cast<size_t>((nt[b] + emd::kMarchTJ - 1) / emd::kMarchTJ) *
-                 ((nr[b] + emd::kMarchMinSeg - 1) / emd::kMarchMinSeg);
   L.units = L.tiles + align256(sizeof(int) * static_cast<size_t>(L.max_tiles));
-  L.misc = L.units + align256(sizeof(int) * max_units);
+  // the march's gather list and its warp partition (up to kMaxMarchWarps + 1 entries)
+  L.misc = L.units + align256(sizeof(int) * (static_cast<size_t>(B) + kMaxMarchWarps + 1));
   L.header = L.misc + 256;
   size_t off = L.header;
   for (int b = 0; b < B; ++b) {
@@ -182,31 +180,52 @@ Layout layout(int B, const int *nt, const int *nr) {
   return L;
 }
 
-// Segments of the marching solve for T marching warps.  When the batch holds at most 64
-// strip-rows per warp, segments are sized so that no warp gets more than one unit (a pass
-// then costs one unit per warp, and a second unit would double it); larger batches get about
-// 16 units per warp, so that whole units leave the warps within about 1/16 of one another.
-// Segments are never shorter than kMarchMinSeg receivers (each carries a 4-row halo).  Fills
-// the gathers' unit fields and the unit -> gather list.
-void march_units(std::vector<Shot> &shots, std::vector<int> &unit_shot, long long T) {
-  long long R = 0;  // strip-rows of the batch
-  for (const Shot &S : shots)
-    R += static_cast<long long>((S.nt + emd::kMarchTJ - 1) / emd::kMarchTJ) * S.nr;
-  T = std::max(1ll, T);
-  const bool one_each = R <= 64 * T;
-  const long long H = std::max<long long>(emd::kMarchMinSeg, one_each ? (R + T - 1) / T : R / (16 * T));
-  unit_shot.clear();
-  for (size_t b = 0; b < shots.size(); ++b) {
+// The marching warps' strip-rows: range[x] .. range[x + 1] for warp x of T.  Up to
+// kMarchAligned strip-rows per warp, each warp gets one whole segment of a strip (segments of
+// one gather of equal height, at least max(kMarchMinRows, rows per warp) each, so none spans
+// two strips and at most T are made); beyond that, T equal contiguous runs.  Also sets each
+// running gather's deciding CTA (the CTA of the warp holding its first strip-row).
+std::vector<int> march_partition(std::vector<Shot> &shots, const std::vector<int> &run, long long R,
+                                 int T, int nw) {
+  std::vector<int> range;
+  range.reserve(T + 1);
+  if (R <= static_cast<long long>(emd::kMarchAligned) * T) {
+    const long long H = std::max<long long>(emd::kMarchMinRows, (R + T - 1) / T);
+    for (int b : run) {
+      const Shot &S = shots[b];
+      const int nseg = static_cast<int>(std::max<long long>(1, S.nr / H));
+      const int seg_h = (S.nr + nseg - 1) / nseg;
+      for (int s = 0; s < S.strips; ++s)
+        for (int i0 = 0; i0 < S.nr; i0 += seg_h) range.push_back(S.march0 + s * S.nr + i0);
+    }
+  } else {
+    for (int x = 0; x < T; ++x) range.push_back(static_cast<int>(x * R / T));
+  }
+  while (static_cast<int>(range.size()) < T) range.push_back(static_cast<int>(R));  // idle warps
+  range.push_back(static_cast<int>(R));
+  for (int b : run) {  // the warp whose range holds the gather's first strip-row
+    const int x = static_cast<int>(std::upper_bound(range.begin(), range.end() - 1, shots[b].march0) -
+                                   range.begin()) - 1;
+    shots[b].march_owner = x / nw;
+  }
+  return range;
+}
+
+// The marching solve's order: each gather's 120-sample strips laid end to end, each strip a
+// column of nr strip-rows.  Fills the gathers' march fields (first strip-row, strip-rows per
+// pass) for the gathers in `run` (the running ones, in order) and returns the strip-rows of
+// one pass, or -1 when they do not fit an int.
+long long march_layout(std::vector<Shot> &shots, const std::vector<int> &run) {
+  long long R = 0;
+  for (int b : run) {
     Shot &S = shots[b];
     S.strips = (S.nt + emd::kMarchTJ - 1) / emd::kMarchTJ;
-    long long nseg = one_each ? S.nr / H : (S.nr + H - 1) / H;
-    nseg = std::max(1ll, std::min<long long>(nseg, (S.nr + emd::kMarchMinSeg - 1) / emd::kMarchMinSeg));
-    S.seg_h = static_cast<int>((S.nr + nseg - 1) / nseg);
-    nseg = (S.nr + S.seg_h - 1) / S.seg_h;
-    S.unit0 = static_cast<int>(unit_shot.size());
-    S.nunits = static_cast<int>(S.strips * nseg);
-    unit_shot.insert(unit_shot.end(), S.nunits, static_cast<int>(b));
+    S.march0 = static_cast<int>(R);
+    S.marchn = S.strips * S.nr;
+    R += S.marchn;
+    if (R > 0x7fffffffll) return -1;
   }
+  return R;
 }
 
 bool params_ok(const emd_params &p) {
@@ -472,9 +491,13 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     nr_max = std::max(nr_max, nr[b]);
   }
   const int grid = static_cast<int>(tile_shot.size());
-  std::vector<int> unit_shot;  // marching solve: its unit list
-  if (sh.solve_march)
-    march_units(shots, unit_shot, static_cast<long long>(sh.nw) * sh.minb * sm_count());
+  std::vector<int> march_run;  // marching solve: the gathers in march order
+  long long march_rows = 0;
+  if (sh.solve_march) {
+    for (int b = 0; b < B; ++b) march_run.push_back(b);
+    march_rows = march_layout(shots, march_run);
+    if (march_rows < 0) return EMD_ERR_ARG;  // more strip-rows than the march counts in an int
+  }
 
   State *states = reinterpret_cast<State *>(base + L.states);
   Shot *dshots = reinterpret_cast<Shot *>(base + L.shots);
@@ -487,9 +510,10 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   EMD_CK(cudaMemcpyAsync(dshots, shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
   EMD_CK(cudaMemcpyAsync(dtiles, tile_shot.data(), sizeof(int) * tile_shot.size(),
                          cudaMemcpyHostToDevice, stream));
-  if (!unit_shot.empty())
-    EMD_CK(cudaMemcpyAsync(dunits, unit_shot.data(), sizeof(int) * unit_shot.size(),
+  if (!march_run.empty())
+    EMD_CK(cudaMemcpyAsync(dunits, march_run.data(), sizeof(int) * march_run.size(),
                            cudaMemcpyHostToDevice, stream));
+  int *drange = dunits + B;  // the marching warps' partition (set at launch)
   EMD_CK(cudaMemsetAsync(states, 0, sizeof(State) * B, stream));
   EMD_CK(cudaMemsetAsync(n_done, 0, 2 * sizeof(int), stream));
   EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double) * emd::kAccBufs * emd::kSpread * emd::kAcc * B,
@@ -513,7 +537,9 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   ctl.states = states;
   ctl.acc = acc;
   ctl.tile_shot = dtiles;
-  ctl.unit_shot = dunits;
+  ctl.march_run = dunits;
+  ctl.march_nrun = static_cast<int>(march_run.size());
+  ctl.march_range = drange;
   ctl.n_done = n_done;
   ctl.error = err_flag;
   ctl.trace = p.trace;
@@ -550,8 +576,6 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   if (!resident && p.launch_mode == 0 && (sh.solve_tma || sh.solve_march)) {
     const bool march = sh.solve_march != nullptr;
     void (*fn)(Ctl, int, int, int) = march ? sh.solve_march : sh.solve_tma;
-    const std::vector<int> &work = march ? unit_shot : tile_shot;  // every gather's work items
-    int *dwork = march ? dunits : dtiles;
     int dev = 0, coop = 0, per_sm = 0;
     const size_t tsmem = solve_smem_bytes(sh);
     const int tthreads = (sh.nw + (march ? 1 : 2)) * 32;
@@ -563,17 +587,30 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
         per_sm >= 1) {
       const long long chunk =
           p.tol > 0.0 && B > 1 ? static_cast<long long>(kRebalance) * p.check_every : p.max_iter;
-      const int cap = std::min(per_sm, sh.minb) * sm_count();  // co-resident CTAs
-      std::vector<int> run;  // the chunk's work list (empty: the full list)
+      int cap = std::min(per_sm, sh.minb) * sm_count();  // co-resident CTAs
+      if (march) cap = std::min(cap, kMaxMarchWarps / sh.nw);  // the partition table's size
+      // the chunk's work: tiles (tile pass) or strip-rows (march) of the running gathers
       std::vector<Shot> run_shots;
+      long long items = march ? march_rows : static_cast<long long>(grid);
+      int dealt = B;  // gathers the current work list was dealt for
+      bool redealt = false, redealt_now = false;
+      std::vector<int> cur_run = march_run;  // the march: running gathers of the current deal
       long long k0 = 0;
       while (k0 < p.max_iter) {
         const int kb = static_cast<int>(k0);
         const int ke = static_cast<int>(std::min<long long>(p.max_iter, k0 + chunk));
-        int items = static_cast<int>(run.empty() ? work.size() : run.size()), kb_ = kb, ke_ = ke;
-        const int cgrid = march ? std::min((items + sh.nw - 1) / sh.nw, cap) : std::min(items, cap);
+        int n_items = static_cast<int>(items), kb_ = kb, ke_ = ke;
+        const int cgrid = march ? cap : std::min(n_items, cap);
+        if (march && (k0 == 0 || redealt_now)) {  // the warps' strip-rows for this deal
+          run_shots = run_shots.empty() ? shots : run_shots;
+          const std::vector<int> range = march_partition(run_shots, cur_run, items, cgrid * sh.nw, sh.nw);
+          EMD_CK(cudaMemcpyAsync(drange, range.data(), sizeof(int) * range.size(), cudaMemcpyHostToDevice,
+                                 stream));
+          EMD_CK(cudaMemcpyAsync(dshots, run_shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
+          redealt_now = false;
+        }
         Ctl cctl = ctl;
-        void *args[] = {&cctl, &items, &kb_, &ke_};
+        void *args[] = {&cctl, &n_items, &kb_, &ke_};
         EMD_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(fn), dim3(cgrid), dim3(tthreads),
                                            args, tsmem, stream));
         persistent = true;
@@ -587,27 +624,38 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
         EMD_CK(cudaMemcpyAsync(h_flags, n_done, sizeof(h_flags), cudaMemcpyDeviceToHost, stream));
         EMD_CK(cudaStreamSynchronize(stream));
         if (h_flags[1] || h_flags[0] >= B) break;
-        std::vector<int> next;
+        std::vector<int> running;
+        for (int b = 0; b < B; ++b)
+          if (!hs[b].done) running.push_back(b);
+        if (static_cast<int>(running.size()) == dealt) continue;  // none stopped since the last deal
+        // some gathers stopped: deal the running ones' work over every CTA again
         run_shots = shots;
-        for (int b = 0; b < B; ++b) {
-          if (hs[b].done) continue;
-          Shot &S = run_shots[b];
-          (march ? S.unit0 : S.tile0) = static_cast<int>(next.size());
-          next.insert(next.end(), march ? S.nunits : S.ntiles, b);
-        }
-        const size_t now = run.empty() ? work.size() : run.size();
-        if (next.size() != now) {  // some gathers stopped: deal the rest over every CTA
-          run.swap(next);
-          EMD_CK(cudaMemcpyAsync(dshots, run_shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice,
+        if (march) {
+          items = march_layout(run_shots, running);
+          ctl.march_nrun = static_cast<int>(running.size());
+          cur_run = running;
+          redealt_now = true;  // partition and shots go out before the next launch
+          EMD_CK(cudaMemcpyAsync(dunits, running.data(), sizeof(int) * running.size(),
+                                 cudaMemcpyHostToDevice, stream));
+        } else {
+          std::vector<int> next;
+          for (int b : running) {
+            run_shots[b].tile0 = static_cast<int>(next.size());
+            next.insert(next.end(), shots[b].ntiles, b);
+          }
+          items = static_cast<long long>(next.size());
+          EMD_CK(cudaMemcpyAsync(dtiles, next.data(), sizeof(int) * next.size(), cudaMemcpyHostToDevice,
                                  stream));
-          EMD_CK(cudaMemcpyAsync(dwork, run.data(), sizeof(int) * run.size(), cudaMemcpyHostToDevice,
-                                 stream));
         }
+        if (!march)
+          EMD_CK(cudaMemcpyAsync(dshots, run_shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
+        dealt = static_cast<int>(running.size());
+        redealt = true;
       }
-      if (!run.empty()) {  // the finalize pass walks every gather's tiles
+      if (redealt) {  // the finalize pass walks every gather's tiles
         EMD_CK(cudaMemcpyAsync(dshots, shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
-        EMD_CK(cudaMemcpyAsync(dwork, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice,
-                               stream));
+        EMD_CK(cudaMemcpyAsync(dtiles, tile_shot.data(), sizeof(int) * tile_shot.size(),
+                               cudaMemcpyHostToDevice, stream));
       }
     }
     (void)cudaGetLastError();

@@ -33,7 +33,8 @@ namespace emd {
 constexpr int kMarchW = 128;    // staged time samples of a strip
 constexpr int kMarchTJ = 120;   // owned time samples of a strip
 constexpr int kFoldRows = 32;   // owned rows summed in FP32 before a fold into FP64
-constexpr int kMarchMinSeg = 8; // fewest receivers in a segment (the halo costs 4 rows)
+constexpr int kMarchMinRows = 8; // fewest strip-rows of a whole-segment range
+constexpr int kMarchAligned = 64; // up to this many strip-rows per warp, ranges are whole segments
 
 // Per-warp shared memory of the march: a ring of D rows of the six input planes, and three
 // rows of scratch for values carried two or three rows back.  Every lane copies, reads and
@@ -306,7 +307,8 @@ __device__ __forceinline__ void march_unit_any(const MarchUnit &m, bool iso, flo
 }
 
 // A gather's pass-k sums of this warp (folded into `mine`) to the gather's accumulators, then
-// its count of finished units with release semantics (it publishes the warp's stores and sums).
+// its count of finished strip-rows with release semantics (it publishes the warp's stores and
+// sums).
 __device__ __forceinline__ void march_flush(const Ctl &c, int g, int n, int k, double &mine, int wid) {
   const int lane = threadIdx.x & 31;
   double *acc = acc_of(c, g, k & 1);
@@ -316,108 +318,132 @@ __device__ __forceinline__ void march_flush(const Ctl &c, int g, int n, int k, d
   if (lane == 0) red_release_add(&c.states[g].tiles_done, static_cast<unsigned>(n));
 }
 
-// Persistent solve by marching warps: passes [k_begin, k_end) of every gather in the unit
-// list, in one cooperative launch.  NW marching warps and one decider warp per CTA; warp w of
-// CTA b marches the contiguous units [lo(b NW + w), lo(b NW + w + 1)) of every pass, with a
-// ring of D rows in flight.
+// The run (index into c.march_run) whose strip-rows contain `pos`: the last run whose first
+// strip-row is <= pos (runs are in march order).
+__device__ __forceinline__ int march_find(const Ctl &c, int pos) {
+  int lo = 0, hi = c.march_nrun - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (c.shots[c.march_run[mid]].march0 <= pos)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Persistent solve by marching warps: passes [k_begin, k_end) of every running gather, in one
+// cooperative launch.  The running gathers' strips, each a column of nr receiver rows, are
+// laid end to end (total_rows strip-rows per pass); marching warp x of the grid takes the
+// contiguous strip-rows [march_range[x], march_range[x + 1]) of every pass and marches them
+// as one segment per strip they touch (a 4-row halo each).  The host partition either
+// balances the warps to one row or, when there are few rows per warp, gives each warp one
+// whole segment of a strip.  NW marching warps and one decider warp per CTA; a ring of D rows
+// in flight per warp.
 template <int NW, int D, int MINB>
 __global__ void __launch_bounds__((NW + 1) * 32, MINB)
-    k_solve_march(Ctl c, int total_units, int k_begin, int k_end) {
+    k_solve_march(Ctl c, int total_rows, int k_begin, int k_end) {
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ float4 dyn4[];
   float *sbase = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(dyn4) + 127u) & ~static_cast<uintptr_t>(127u));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int T = gridDim.x * NW;  // marching warps in the grid
+  (void)total_rows;  // the partition's end, march_range[gridDim.x NW]
 
-  if (warp == NW) {  // ---- decider warp: decisions of the gathers whose first unit is here
-    const int lo = tile_lo(blockIdx.x * NW, total_units, T), hi = tile_lo((blockIdx.x + 1) * NW, total_units, T);
+  if (warp == NW) {  // ---- decider warp: decisions of the gathers the host assigned to this CTA
+    const int lo = c.march_range[blockIdx.x * NW], hi = c.march_range[(blockIdx.x + 1) * NW];
     if (lo >= hi) return;
     decider_loop(
-        c, c.unit_shot[lo], c.unit_shot[hi - 1], k_begin, k_end,
-        [&](const Shot &S) { return tile_owner(S.unit0, total_units, T) / NW == static_cast<int>(blockIdx.x); },
-        [](const Shot &S) { return S.nunits; });
+        c, c.march_run[march_find(c, lo)], c.march_run[march_find(c, hi - 1)], k_begin, k_end,
+        [&](const Shot &S) { return S.march_owner == static_cast<int>(blockIdx.x); },
+        [](const Shot &S) { return S.marchn; });
     return;
   }
 
   // ---- marching warp
   float *ring = sbase + warp * MarchRing<D>::WARP;
   const int wid = blockIdx.x * NW + warp;
-  const int u_lo = tile_lo(wid, total_units, T), u_hi = tile_lo(wid + 1, total_units, T);
-  if (u_lo >= u_hi) return;
+  const int r_lo = c.march_range[wid], r_hi = c.march_range[wid + 1];
+  if (r_lo >= r_hi) return;
+  const int run_lo = march_find(c, r_lo);
   float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   double mine = 0.0;
   for (int k = k_begin; k < k_end; ++k) {
-    int g_cur = -1, n_cur = 0;
-    bool live = false, any = false;
-    MarchUnit m;
-    for (int u = u_lo; u < u_hi; ++u) {
-      const int g = c.unit_shot[u];
+    bool any = false;
+    int pos = r_lo;
+    for (int run = run_lo; pos < r_hi; ++run) {
+      const int g = c.march_run[run];
       const Shot &S = c.shots[g];
       State *sp = c.states + g;
-      const int lu = u - S.unit0, seg = lu / S.strips;
-      m.i0 = seg * S.seg_h;
-      m.h = min(S.seg_h, S.nr - m.i0);
-      m.j0 = (lu - seg * S.strips) * kMarchTJ;
-      if (g != g_cur) {
-        if (n_cur > 0) march_flush(c, g_cur, n_cur, k, mine, wid);
-        g_cur = g;
-        n_cur = 0;
-        // pass k - 1 of the gather is complete (its rows feed these copies); every lane waits
-        bool ok = __all_sync(FULL, wait_counter(&sp->tiles_done,
-                                                static_cast<unsigned>(k) * static_cast<unsigned>(S.nunits),
-                                                &sp->done));
-        if (!ok) {
-          if (lane == 0) atomicExch(c.error, 1);
-          return;
-        }
-        live = __shfl_sync(FULL, ld_acquire_int(&sp->done), 0) == 0;
-        if (!live) continue;
-        const int kp = k == 0 ? 0 : (k - 1) % 3, kc = k % 3;
-        m.nr = S.nr;
-        m.nt = S.nt;
-        m.ntp = S.ntp;
-        m.rdx = S.rdx;
-        m.rdt = S.rdt;
-        m.ax = S.ux[kp];
-        m.at = S.ut[kp];
-        m.bx = S.ux[kc];
-        m.bt = S.ut[kc];
-        m.ph_prev = S.ph[(k + 1) & 1];
-        m.f = S.f;
-        m.ph_cur = S.ph[k & 1];
-        m.uxn = S.ux[(k + 1) % 3];
-        m.utn = S.ut[(k + 1) % 3];
-        m.need_res = (c.tol > 0.0 && (k + 1) % c.check_every == 0) || k + 1 >= c.max_iter;
-        march_prefetch<D>(m, ring);
-        // decision k - 1 (the copies above overlap it)
-        ok = __all_sync(FULL, wait_counter(&sp->epoch, static_cast<unsigned>(k), &sp->done));
-        if (!ok) {
-          cp_async_wait<0>();
-          if (lane == 0) atomicExch(c.error, 1);
-          return;
-        }
-        const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(sp));
-        const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(sp) + 1);
-        live = __shfl_sync(FULL, h0.y, 0) == 0;
-        if (!live) {
-          cp_async_wait<0>();  // the gather stopped: let the staged rows land unused
-          continue;
-        }
-        any = true;
-        m.alpha = __int_as_float(h0.z);
-        m.coef = __int_as_float(h0.w);
-        m.theta = __int_as_float(h1.x);
-        m.inv = __int_as_float(h1.y);
-        m.fmean = __int_as_float(h1.z);
-      } else {
-        if (!live) continue;
+      const int end = min(r_hi, S.march0 + S.marchn);  // this warp's strip-rows of gather g
+      const int n_rows = end - pos;
+      // pass k - 1 of the gather is complete (its rows feed these copies); every lane waits
+      bool ok = __all_sync(FULL, wait_counter(&sp->tiles_done,
+                                              static_cast<unsigned>(k) * static_cast<unsigned>(S.marchn),
+                                              &sp->done));
+      if (!ok) {
+        if (lane == 0) atomicExch(c.error, 1);
+        return;
+      }
+      if (__shfl_sync(FULL, ld_acquire_int(&sp->done), 0)) {  // stopped: skip its rows
+        pos = end;
+        continue;
+      }
+      const int kp = k == 0 ? 0 : (k - 1) % 3, kc = k % 3;
+      MarchUnit m;
+      m.nr = S.nr;
+      m.nt = S.nt;
+      m.ntp = S.ntp;
+      m.rdx = S.rdx;
+      m.rdt = S.rdt;
+      m.ax = S.ux[kp];
+      m.at = S.ut[kp];
+      m.bx = S.ux[kc];
+      m.bt = S.ut[kc];
+      m.ph_prev = S.ph[(k + 1) & 1];
+      m.f = S.f;
+      m.ph_cur = S.ph[k & 1];
+      m.uxn = S.ux[(k + 1) % 3];
+      m.utn = S.ut[(k + 1) % 3];
+      m.need_res = (c.tol > 0.0 && (k + 1) % c.check_every == 0) || k + 1 >= c.max_iter;
+      // the first segment's rows start loading while decision k - 1 is awaited
+      int local = pos - S.march0, strip = local / S.nr;
+      m.j0 = strip * kMarchTJ;
+      m.i0 = local - strip * S.nr;
+      m.h = min(S.nr - m.i0, end - pos);
+      march_prefetch<D>(m, ring);
+      ok = __all_sync(FULL, wait_counter(&sp->epoch, static_cast<unsigned>(k), &sp->done));
+      if (!ok) {
+        cp_async_wait<0>();
+        if (lane == 0) atomicExch(c.error, 1);
+        return;
+      }
+      const int4 h0 = __ldcg(reinterpret_cast<const int4 *>(sp));
+      const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(sp) + 1);
+      if (__shfl_sync(FULL, h0.y, 0)) {  // decision k - 1 stopped the gather
+        cp_async_wait<0>();               // let the staged rows land unused
+        pos = end;
+        continue;
+      }
+      any = true;
+      m.alpha = __int_as_float(h0.z);
+      m.coef = __int_as_float(h0.w);
+      m.theta = __int_as_float(h1.x);
+      m.inv = __int_as_float(h1.y);
+      m.fmean = __int_as_float(h1.z);
+      while (true) {  // one segment per strip of gather g in [pos, end)
+        march_unit_any<D>(m, c.iso != 0, ring, v, mine);
+        pos += m.h;
+        if (pos >= end) break;
+        local = pos - S.march0;
+        strip = local / S.nr;
+        m.j0 = strip * kMarchTJ;
+        m.i0 = local - strip * S.nr;
+        m.h = min(S.nr - m.i0, end - pos);
         march_prefetch<D>(m, ring);
       }
-      march_unit_any<D>(m, c.iso != 0, ring, v, mine);
-      ++n_cur;
+      march_flush(c, g, n_rows, k, mine, wid);
     }
-    if (n_cur > 0) march_flush(c, g_cur, n_cur, k, mine, wid);
     if (!any) {
       cp_async_wait<0>();
       return;  // every gather this warp marches has stopped
