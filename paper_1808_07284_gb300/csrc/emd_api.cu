@@ -86,7 +86,6 @@ const Shape kShapes[] = {EMD_SHAPE(16, 128),          EMD_SHAPE(8, 128),
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 constexpr int kTmaShape = 6;         // 13 x 120, two CTAs per SM: the untuned default
 constexpr int kTmaFirst = 6;         // shapes kTmaFirst .. kNumShapes - 1 run persistent solves
-constexpr int kMaxMarchWarps = 16384;  // most marching warps a launch may hold (partition table)
 
 // Dynamic shared memory of the plain pass / finalize pass of a shape, of its per-pass
 // TMA kernel (two stages of six (TI + 4) x 128 planes, plus alignment slack) and of its
@@ -166,8 +165,7 @@ Layout layout(int B, const int *nt, const int *nr) {
   L.acc = L.shots + align256(sizeof(Shot) * B);
   L.tiles = L.acc + align256(sizeof(double) * emd::kAccBufs * emd::kSpread * emd::kAcc * B);
   L.units = L.tiles + align256(sizeof(int) * static_cast<size_t>(L.max_tiles));
-  // the march's gather list and its warp partition (up to kMaxMarchWarps + 1 entries)
-  L.misc = L.units + align256(sizeof(int) * (static_cast<size_t>(B) + kMaxMarchWarps + 1));
+  L.misc = L.units + align256(sizeof(int) * static_cast<size_t>(B));  // the march's gather list
   L.header = L.misc + 256;
   size_t off = L.header;
   for (int b = 0; b < B; ++b) {
@@ -180,52 +178,61 @@ Layout layout(int B, const int *nt, const int *nr) {
   return L;
 }
 
-// The marching warps' strip-rows: range[x] .. range[x + 1] for warp x of T.  Up to
-// kMarchAligned strip-rows per warp, each warp gets one whole segment of a strip (segments of
-// one gather of equal height, at least max(kMarchMinRows, rows per warp) each, so none spans
-// two strips and at most T are made); beyond that, T equal contiguous runs.  Also sets each
-// running gather's deciding CTA (the CTA of the warp holding its first strip-row).
-std::vector<int> march_partition(std::vector<Shot> &shots, const std::vector<int> &run, long long R,
-                                 int T, int nw) {
-  std::vector<int> range;
-  range.reserve(T + 1);
-  if (R <= static_cast<long long>(emd::kMarchAligned) * T) {
-    const long long H = std::max<long long>(emd::kMarchMinRows, (R + T - 1) / T);
-    for (int b : run) {
-      const Shot &S = shots[b];
-      const int nseg = static_cast<int>(std::max<long long>(1, S.nr / H));
-      const int seg_h = (S.nr + nseg - 1) / nseg;
-      for (int s = 0; s < S.strips; ++s)
-        for (int i0 = 0; i0 < S.nr; i0 += seg_h) range.push_back(S.march0 + s * S.nr + i0);
-    }
-  } else {
-    for (int x = 0; x < T; ++x) range.push_back(static_cast<int>(x * R / T));
-  }
-  while (static_cast<int>(range.size()) < T) range.push_back(static_cast<int>(R));  // idle warps
-  range.push_back(static_cast<int>(R));
-  for (int b : run) {  // the warp whose range holds the gather's first strip-row
-    const int x = static_cast<int>(std::upper_bound(range.begin(), range.end() - 1, shots[b].march0) -
-                                   range.begin()) - 1;
-    shots[b].march_owner = x / nw;
-  }
-  return range;
-}
-
-// The marching solve's order: each gather's 120-sample strips laid end to end, each strip a
-// column of nr strip-rows.  Fills the gathers' march fields (first strip-row, strip-rows per
-// pass) for the gathers in `run` (the running ones, in order) and returns the strip-rows of
-// one pass, or -1 when they do not fit an int.
-long long march_layout(std::vector<Shot> &shots, const std::vector<int> &run) {
-  long long R = 0;
+// Units of the marching solve for T marching warps, dealt round-robin (unit u to warp
+// u mod T).  Every running gather is cut into segments of about H receivers (nseg = ceil(nr /
+// H) equal segments) times its 120-sample strips; the warp marching the most units then
+// needs ceil(U / T) (h + 4 + c0) row times (4 halo rows, c0 ~ 2 rows to start a unit), and H
+// is the candidate that minimises it.  Fills the gathers' unit fields and deciding CTAs (the
+// CTA of the warp that marches a gather's first unit); returns the units of one pass, or -1
+// when they do not fit an int.
+long long march_layout(std::vector<Shot> &shots, const std::vector<int> &run, long long T, int nw) {
+  constexpr long long kStartRows = 2;
+  int nr_max = 1;
   for (int b : run) {
     Shot &S = shots[b];
     S.strips = (S.nt + emd::kMarchTJ - 1) / emd::kMarchTJ;
-    S.march0 = static_cast<int>(R);
-    S.marchn = S.strips * S.nr;
-    R += S.marchn;
-    if (R > 0x7fffffffll) return -1;
+    nr_max = std::max(nr_max, S.nr);
   }
-  return R;
+  auto units_for = [&](long long H, long long &hmax) {
+    long long U = 0;
+    hmax = 0;
+    for (int b : run) {
+      const Shot &S = shots[b];
+      const long long nseg = (S.nr + H - 1) / H;
+      hmax = std::max(hmax, (S.nr + nseg - 1) / nseg);
+      U += S.strips * nseg;
+    }
+    return U;
+  };
+  long long best_H = nr_max, best_cost = -1;
+  const int cands = std::min(512, std::max(1, (nr_max + emd::kMarchMinSeg - 1) / emd::kMarchMinSeg));
+  for (int c = 1; c <= cands; ++c) {
+    const long long nseg = std::max<long long>(
+        1, static_cast<long long>(std::llround(std::pow(static_cast<double>(nr_max) / emd::kMarchMinSeg,
+                                                        (c - 1.0) / std::max(1, cands - 1)))));
+    const long long H = std::max<long long>(emd::kMarchMinSeg, (nr_max + nseg - 1) / nseg);
+    long long hmax = 0;
+    const long long U = units_for(H, hmax);
+    if (U > 0x7fffffffll) continue;
+    const long long cost = (U + T - 1) / T * (hmax + 4 + kStartRows);
+    if (best_cost < 0 || cost < best_cost || (cost == best_cost && H > best_H)) {
+      best_cost = cost;
+      best_H = H;
+    }
+  }
+  long long U = 0;
+  for (int b : run) {
+    Shot &S = shots[b];
+    const long long nseg = (S.nr + best_H - 1) / best_H;
+    S.seg_h = static_cast<int>((S.nr + nseg - 1) / nseg);
+    const long long ns = (S.nr + S.seg_h - 1) / S.seg_h;
+    S.unit0 = static_cast<int>(U);
+    S.nunits = static_cast<int>(S.strips * ns);
+    S.march_owner = static_cast<int>((U % T) / nw);
+    U += S.nunits;
+    if (U > 0x7fffffffll) return -1;
+  }
+  return U;
 }
 
 bool params_ok(const emd_params &p) {
@@ -491,13 +498,9 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
     nr_max = std::max(nr_max, nr[b]);
   }
   const int grid = static_cast<int>(tile_shot.size());
-  std::vector<int> march_run;  // marching solve: the gathers in march order
-  long long march_rows = 0;
-  if (sh.solve_march) {
+  std::vector<int> march_run;  // marching solve: the gathers in march order (laid out at launch)
+  if (sh.solve_march)
     for (int b = 0; b < B; ++b) march_run.push_back(b);
-    march_rows = march_layout(shots, march_run);
-    if (march_rows < 0) return EMD_ERR_ARG;  // more strip-rows than the march counts in an int
-  }
 
   State *states = reinterpret_cast<State *>(base + L.states);
   Shot *dshots = reinterpret_cast<Shot *>(base + L.shots);
@@ -513,7 +516,6 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   if (!march_run.empty())
     EMD_CK(cudaMemcpyAsync(dunits, march_run.data(), sizeof(int) * march_run.size(),
                            cudaMemcpyHostToDevice, stream));
-  int *drange = dunits + B;  // the marching warps' partition (set at launch)
   EMD_CK(cudaMemsetAsync(states, 0, sizeof(State) * B, stream));
   EMD_CK(cudaMemsetAsync(n_done, 0, 2 * sizeof(int), stream));
   EMD_CK(cudaMemsetAsync(acc, 0, sizeof(double) * emd::kAccBufs * emd::kSpread * emd::kAcc * B,
@@ -539,7 +541,6 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   ctl.tile_shot = dtiles;
   ctl.march_run = dunits;
   ctl.march_nrun = static_cast<int>(march_run.size());
-  ctl.march_range = drange;
   ctl.n_done = n_done;
   ctl.error = err_flag;
   ctl.trace = p.trace;
@@ -587,27 +588,24 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
         per_sm >= 1) {
       const long long chunk =
           p.tol > 0.0 && B > 1 ? static_cast<long long>(kRebalance) * p.check_every : p.max_iter;
-      int cap = std::min(per_sm, sh.minb) * sm_count();  // co-resident CTAs
-      if (march) cap = std::min(cap, kMaxMarchWarps / sh.nw);  // the partition table's size
+      const int cap = std::min(per_sm, sh.minb) * sm_count();  // co-resident CTAs
       // the chunk's work: tiles (tile pass) or strip-rows (march) of the running gathers
       std::vector<Shot> run_shots;
-      long long items = march ? march_rows : static_cast<long long>(grid);
+      long long items = static_cast<long long>(grid);  // the march's units are counted at launch
       int dealt = B;  // gathers the current work list was dealt for
-      bool redealt = false, redealt_now = false;
-      std::vector<int> cur_run = march_run;  // the march: running gathers of the current deal
+      bool redealt = false;
       long long k0 = 0;
       while (k0 < p.max_iter) {
         const int kb = static_cast<int>(k0);
         const int ke = static_cast<int>(std::min<long long>(p.max_iter, k0 + chunk));
         int n_items = static_cast<int>(items), kb_ = kb, ke_ = ke;
         const int cgrid = march ? cap : std::min(n_items, cap);
-        if (march && (k0 == 0 || redealt_now)) {  // the warps' strip-rows for this deal
-          run_shots = run_shots.empty() ? shots : run_shots;
-          const std::vector<int> range = march_partition(run_shots, cur_run, items, cgrid * sh.nw, sh.nw);
-          EMD_CK(cudaMemcpyAsync(drange, range.data(), sizeof(int) * range.size(), cudaMemcpyHostToDevice,
-                                 stream));
+        if (march && k0 == 0) {  // the units of the first deal and their warps
+          run_shots = shots;
+          items = march_layout(run_shots, march_run, static_cast<long long>(cgrid) * sh.nw, sh.nw);
+          if (items < 0) return EMD_ERR_ARG;  // more units than an int counts
+          n_items = static_cast<int>(items);
           EMD_CK(cudaMemcpyAsync(dshots, run_shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
-          redealt_now = false;
         }
         Ctl cctl = ctl;
         void *args[] = {&cctl, &n_items, &kb_, &ke_};
@@ -631,12 +629,15 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
         // some gathers stopped: deal the running ones' work over every CTA again
         run_shots = shots;
         if (march) {
-          items = march_layout(run_shots, running);
+          // a new layout changes the gathers' units per pass: their cumulative counts of
+          // finished units restart from k0 times the new count (no kernel is running now)
+          items = march_layout(run_shots, running, static_cast<long long>(cap) * sh.nw, sh.nw);
+          if (items < 0) return EMD_ERR_ARG;
+          for (int b : running) hs[b].tiles_done = static_cast<unsigned>(k0) * static_cast<unsigned>(run_shots[b].nunits);
           ctl.march_nrun = static_cast<int>(running.size());
-          cur_run = running;
-          redealt_now = true;  // partition and shots go out before the next launch
           EMD_CK(cudaMemcpyAsync(dunits, running.data(), sizeof(int) * running.size(),
                                  cudaMemcpyHostToDevice, stream));
+          EMD_CK(cudaMemcpyAsync(states, hs.data(), sizeof(State) * B, cudaMemcpyHostToDevice, stream));
         } else {
           std::vector<int> next;
           for (int b : running) {
@@ -647,8 +648,7 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
           EMD_CK(cudaMemcpyAsync(dtiles, next.data(), sizeof(int) * next.size(), cudaMemcpyHostToDevice,
                                  stream));
         }
-        if (!march)
-          EMD_CK(cudaMemcpyAsync(dshots, run_shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
+        EMD_CK(cudaMemcpyAsync(dshots, run_shots.data(), sizeof(Shot) * B, cudaMemcpyHostToDevice, stream));
         dealt = static_cast<int>(running.size());
         redealt = true;
       }

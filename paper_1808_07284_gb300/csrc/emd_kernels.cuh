@@ -48,9 +48,8 @@ struct Shot {
   float *ph[2];                     // phi^m lives in ph[m & 1], pitched
   int nt, nr, ntp, tiles_j;         // ntp: row pitch in floats (multiple of 32)
   int tile0, ntiles;                // first global tile index and tile count of this gather
-  int march0, marchn;               // marching pass: first strip-row in the march order, and
-                                    // strip-rows per pass (strips x nr)
-  int strips;                       // marching pass: 120-sample strips
+  int unit0, nunits;                // marching pass: first unit in the march order, units per pass
+  int strips, seg_h;                // marching pass: 120-sample strips, receivers per segment
   int march_owner;                  // marching pass: the CTA whose decider warp decides it
   float rdx, rdt;                   // 1/dx (0 when nr == 1), 1/dt
   double area, lambda;              // dx*dt (dt when nr == 1); 4/dx^2 + 4/dt^2
@@ -89,8 +88,6 @@ struct Ctl {
   const int *tile_shot;             // global tile -> gather
   const int *march_run;             // marching pass: the running gathers, in march order
   int march_nrun;                   // ... and how many
-  const int *march_range;           // marching pass: warp x marches strip-rows
-                                    // [march_range[x], march_range[x + 1])
   int *n_done;                      // gathers finished
   int *error;                       // set to 1 when a bounded device wait gives up
   double *trace;                    // optional [gather][max_iter][4] history (or null)

@@ -33,8 +33,7 @@ namespace emd {
 constexpr int kMarchW = 128;    // staged time samples of a strip
 constexpr int kMarchTJ = 120;   // owned time samples of a strip
 constexpr int kFoldRows = 32;   // owned rows summed in FP32 before a fold into FP64
-constexpr int kMarchMinRows = 8; // fewest strip-rows of a whole-segment range
-constexpr int kMarchAligned = 64; // up to this many strip-rows per warp, ranges are whole segments
+constexpr int kMarchMinSeg = 8; // fewest receivers in a segment (each carries a 4-row halo)
 
 // Per-warp shared memory of the march: a ring of D rows of the six input planes, and three
 // rows of scratch for values carried two or three rows back.  Every lane copies, reads and
@@ -307,8 +306,7 @@ __device__ __forceinline__ void march_unit_any(const MarchUnit &m, bool iso, flo
 }
 
 // A gather's pass-k sums of this warp (folded into `mine`) to the gather's accumulators, then
-// its count of finished strip-rows with release semantics (it publishes the warp's stores and
-// sums).
+// its count of finished units with release semantics (it publishes the warp's stores and sums).
 __device__ __forceinline__ void march_flush(const Ctl &c, int g, int n, int k, double &mine, int wid) {
   const int lane = threadIdx.x & 31;
   double *acc = acc_of(c, g, k & 1);
@@ -318,13 +316,13 @@ __device__ __forceinline__ void march_flush(const Ctl &c, int g, int n, int k, d
   if (lane == 0) red_release_add(&c.states[g].tiles_done, static_cast<unsigned>(n));
 }
 
-// The run (index into c.march_run) whose strip-rows contain `pos`: the last run whose first
-// strip-row is <= pos (runs are in march order).
-__device__ __forceinline__ int march_find(const Ctl &c, int pos) {
+// The run (index into c.march_run) whose units contain unit u: the last run whose first
+// unit is <= u (runs are in march order).
+__device__ __forceinline__ int march_find(const Ctl &c, int u) {
   int lo = 0, hi = c.march_nrun - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (c.shots[c.march_run[mid]].march0 <= pos)
+    if (c.shots[c.march_run[mid]].unit0 <= u)
       lo = mid;
     else
       hi = mid - 1;
@@ -333,64 +331,63 @@ __device__ __forceinline__ int march_find(const Ctl &c, int pos) {
 }
 
 // Persistent solve by marching warps: passes [k_begin, k_end) of every running gather, in one
-// cooperative launch.  The running gathers' strips, each a column of nr receiver rows, are
-// laid end to end (total_rows strip-rows per pass); marching warp x of the grid takes the
-// contiguous strip-rows [march_range[x], march_range[x + 1]) of every pass and marches them
-// as one segment per strip they touch (a 4-row halo each).  The host partition either
-// balances the warps to one row or, when there are few rows per warp, gives each warp one
-// whole segment of a strip.  NW marching warps and one decider warp per CTA; a ring of D rows
-// in flight per warp.
+// cooperative launch.  A gather's work is cut into units -- one segment of seg_h receivers of
+// one 120-sample strip -- ordered segment by segment with the strip index fastest, and the
+// running gathers' units are laid end to end (total_units per pass).  Marching warp x of the
+// T in the grid takes units x, x + T, x + 2T, ...: at every step the warps march horizontally
+// adjacent strips of the same segment side by side, so the DRAM bursts their halo columns
+// share are fetched once, and each gather's units of a pass sit at the same position of
+// every warp's sequence, so gathers pass through the grid one behind the other without a
+// grid-wide wait.  NW marching warps and one decider warp per CTA; a ring of D rows in flight
+// per warp.
 template <int NW, int D, int MINB>
 __global__ void __launch_bounds__((NW + 1) * 32, MINB)
-    k_solve_march(Ctl c, int total_rows, int k_begin, int k_end) {
+    k_solve_march(Ctl c, int total_units, int k_begin, int k_end) {
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ float4 dyn4[];
   float *sbase = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(dyn4) + 127u) & ~static_cast<uintptr_t>(127u));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  (void)total_rows;  // the partition's end, march_range[gridDim.x NW]
+  const int T = gridDim.x * NW;  // marching warps in the grid
 
   if (warp == NW) {  // ---- decider warp: decisions of the gathers the host assigned to this CTA
-    const int lo = c.march_range[blockIdx.x * NW], hi = c.march_range[(blockIdx.x + 1) * NW];
-    if (lo >= hi) return;
     decider_loop(
-        c, c.march_run[march_find(c, lo)], c.march_run[march_find(c, hi - 1)], k_begin, k_end,
+        c, 0, c.march_run[c.march_nrun - 1], k_begin, k_end,
         [&](const Shot &S) { return S.march_owner == static_cast<int>(blockIdx.x); },
-        [](const Shot &S) { return S.marchn; });
+        [](const Shot &S) { return S.nunits; });
     return;
   }
 
   // ---- marching warp
   float *ring = sbase + warp * MarchRing<D>::WARP;
   const int wid = blockIdx.x * NW + warp;
-  const int r_lo = c.march_range[wid], r_hi = c.march_range[wid + 1];
-  if (r_lo >= r_hi) return;
-  const int run_lo = march_find(c, r_lo);
+  if (wid >= total_units) return;
+  const int run_first = march_find(c, wid);
   float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   double mine = 0.0;
   for (int k = k_begin; k < k_end; ++k) {
     bool any = false;
-    int pos = r_lo;
-    for (int run = run_lo; pos < r_hi; ++run) {
+    int run = run_first;
+    for (int u = wid; u < total_units; u += T) {
+      while (run + 1 < c.march_nrun && c.shots[c.march_run[run + 1]].unit0 <= u) ++run;
       const int g = c.march_run[run];
       const Shot &S = c.shots[g];
       State *sp = c.states + g;
-      const int end = min(r_hi, S.march0 + S.marchn);  // this warp's strip-rows of gather g
-      const int n_rows = end - pos;
       // pass k - 1 of the gather is complete (its rows feed these copies); every lane waits
       bool ok = __all_sync(FULL, wait_counter(&sp->tiles_done,
-                                              static_cast<unsigned>(k) * static_cast<unsigned>(S.marchn),
+                                              static_cast<unsigned>(k) * static_cast<unsigned>(S.nunits),
                                               &sp->done));
       if (!ok) {
         if (lane == 0) atomicExch(c.error, 1);
         return;
       }
-      if (__shfl_sync(FULL, ld_acquire_int(&sp->done), 0)) {  // stopped: skip its rows
-        pos = end;
-        continue;
-      }
+      if (__shfl_sync(FULL, ld_acquire_int(&sp->done), 0)) continue;  // stopped
+      const int lu = u - S.unit0, seg = lu / S.strips;
       const int kp = k == 0 ? 0 : (k - 1) % 3, kc = k % 3;
       MarchUnit m;
+      m.i0 = seg * S.seg_h;
+      m.h = min(S.seg_h, S.nr - m.i0);
+      m.j0 = (lu - seg * S.strips) * kMarchTJ;
       m.nr = S.nr;
       m.nt = S.nt;
       m.ntp = S.ntp;
@@ -406,12 +403,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
       m.uxn = S.ux[(k + 1) % 3];
       m.utn = S.ut[(k + 1) % 3];
       m.need_res = (c.tol > 0.0 && (k + 1) % c.check_every == 0) || k + 1 >= c.max_iter;
-      // the first segment's rows start loading while decision k - 1 is awaited
-      int local = pos - S.march0, strip = local / S.nr;
-      m.j0 = strip * kMarchTJ;
-      m.i0 = local - strip * S.nr;
-      m.h = min(S.nr - m.i0, end - pos);
-      march_prefetch<D>(m, ring);
+      march_prefetch<D>(m, ring);  // the unit's first rows load while decision k - 1 is awaited
       ok = __all_sync(FULL, wait_counter(&sp->epoch, static_cast<unsigned>(k), &sp->done));
       if (!ok) {
         cp_async_wait<0>();
@@ -422,7 +414,6 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
       const int4 h1 = __ldcg(reinterpret_cast<const int4 *>(sp) + 1);
       if (__shfl_sync(FULL, h0.y, 0)) {  // decision k - 1 stopped the gather
         cp_async_wait<0>();               // let the staged rows land unused
-        pos = end;
         continue;
       }
       any = true;
@@ -431,18 +422,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
       m.theta = __int_as_float(h1.x);
       m.inv = __int_as_float(h1.y);
       m.fmean = __int_as_float(h1.z);
-      while (true) {  // one segment per strip of gather g in [pos, end)
-        march_unit_any<D>(m, c.iso != 0, ring, v, mine);
-        pos += m.h;
-        if (pos >= end) break;
-        local = pos - S.march0;
-        strip = local / S.nr;
-        m.j0 = strip * kMarchTJ;
-        m.i0 = local - strip * S.nr;
-        m.h = min(S.nr - m.i0, end - pos);
-        march_prefetch<D>(m, ring);
-      }
-      march_flush(c, g, n_rows, k, mine, wid);
+      march_unit_any<D>(m, c.iso != 0, ring, v, mine);
+      march_flush(c, g, 1, k, mine, wid);
     }
     if (!any) {
       cp_async_wait<0>();
