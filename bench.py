@@ -142,8 +142,9 @@ def _kernel_of(tile):
 
 def _traffic(name, cells):
     """DRAM bytes per pass for `cells` cells from a committed ncu summary of the same kernel
-    sources (scaled by cells when the capture ran a smaller case of the same gathers), or
-    None when it was taken from other sources."""
+    sources and tile shape, captured on fewer shots of the same gathers and scaled by cells
+    (the bytes of a pass grow with the cells it updates), or None when the summary was taken
+    from other sources."""
     try:
         with open(os.path.join(ROOT, "profiles", name)) as fh:
             t = json.load(fh)
@@ -404,7 +405,7 @@ def run_marine(a):
     peak, peak_kind = _peaks()
     achieved = CELL_BYTES * cells / t_pass / 1e9
     kname, kargs = _kernel_of(res[0].tile)
-    traffic = _traffic(f"{kname}_traffic_marine.json", cells)
+    traffic = _traffic(f"{kname}_tile{res[0].tile}_traffic_marine.json", cells)
 
     # ---- end to end through the public API: pinned host gathers in, adjoint sources out
     h_obs = [torch.from_numpy(o).pin_memory() for o, _ in pairs]
