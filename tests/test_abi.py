@@ -171,3 +171,30 @@ def test_product_path_has_no_oracle_or_fallback():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+(oracle|synth)\b", text, flags=re.M), f
+
+
+def test_batched_adjoint_argument_errors_need_no_gpu(B):
+    """emd_adjoint_batched refuses bad sizes, spacings, balance, null pointers and a short or
+    misaligned workspace before any CUDA call."""
+    L = B.lib()
+    P2, I2, D2 = ctypes.c_void_p * 2, ctypes.c_int * 2, ctypes.c_double * 2
+    phis, gps = P2(256, 512), P2(768, 1024)
+    nbytes = B.emd_batched_adjoint_workspace_size(2)
+    assert B.emd_batched_adjoint_workspace_size(0) == 0 and nbytes >= 2 * 8
+    fake = ctypes.c_void_p(256)
+
+    def call(Bn=2, phi=phis, nt=(8, 8), nr=(4, 4), dt=(1e-3, 1e-3), dx=(10.0, 10.0), bal=1, gp=gps,
+             ws=fake, n=nbytes):
+        return L.emd_adjoint_batched(Bn, phi, I2(*nt), I2(*nr), D2(*dt), D2(*dx), bal, None, gp, None, ws, n,
+                                     None)
+
+    assert call(Bn=0) == B.EMD_ERR_ARG
+    assert call(bal=3) == B.EMD_ERR_ARG
+    assert call(phi=P2(256, None)) == B.EMD_ERR_ARG
+    assert call(gp=P2(None, 512)) == B.EMD_ERR_ARG
+    assert call(nt=(8, 1)) == B.EMD_ERR_ARG
+    assert call(dt=(1e-3, 0.0)) == B.EMD_ERR_ARG
+    assert call(dx=(float("nan"), 10.0)) == B.EMD_ERR_ARG
+    assert call(n=nbytes - 8) == B.EMD_ERR_WORKSPACE
+    assert call(ws=ctypes.c_void_p(264)) == B.EMD_ERR_WORKSPACE
+    assert call(ws=None) == B.EMD_ERR_WORKSPACE
