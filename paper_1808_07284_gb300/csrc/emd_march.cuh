@@ -22,8 +22,8 @@
 // and ran 3.7-4.7 times slower than the tile pass; it is not built.)
 //
 // Sums: FP32 within a lane over at most kFoldRows owned rows, then a warp sum per value
-// folded into an FP64 accumulator (lane q holds value q); at the end of a gather's units in a
-// pass the nine FP64 values go to the gather's accumulators by FP64 atomics.
+// folded into an FP64 accumulator (lane q holds value q); at the end of every unit the FP64
+// values go to the gather's accumulators by FP64 atomics.
 #pragma once
 
 #include "emd_pass_tma.cuh"
@@ -44,12 +44,6 @@ struct MarchRing {
   static constexpr int SCRATCH = 3 * kMarchW;       // phi^k of row r - 2, p_k and q_k of row r - 3
   static constexpr int WARP = D * ROW + SCRATCH;    // floats per warp
 };
-
-// Shared memory of a k_solve_march CTA.
-template <int NW, int D>
-constexpr size_t march_smem_bytes() {
-  return static_cast<size_t>(NW) * MarchRing<D>::WARP * 4u + 128u;
-}
 
 // The unit a warp marches: geometry, planes and this pass's step sizes.
 struct MarchUnit {

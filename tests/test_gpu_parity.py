@@ -163,18 +163,23 @@ def test_small_gather_normalised_domain(pkg):
 SHAPES = [(1, 2), (1, 37), (2, 2), (3, 5), (17, 130), (33, 251), (9, 1000), (40, 121)]
 
 
+@pytest.mark.parametrize("tile", [0, 10])
 @pytest.mark.parametrize("nr,nt", SHAPES)
-def test_ragged_shapes(pkg, nr, nt):
+def test_ragged_shapes(pkg, nr, nt, tile):
+    """Ragged and degenerate grids (one receiver, two samples, a partial last strip) with
+    the automatic choice and with the marching solve forced."""
     rng = np.random.default_rng(nr * 1000 + nt)
     obs, pred = synth.gather_pair_hyperbolic(nt=max(nt, 8), nr=nr, dt=2e-3, seed=nr + nt)
     obs, pred = obs[:, :nt].copy(), pred[:, :nt].copy()
     pred += 0.05 * rng.standard_normal(pred.shape).astype(np.float32)
     r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150)
-    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=150)
+    g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=150, tile=tile)
     assert_parity(g, r)
+    if tile:
+        assert g["info"]["tile"] == tile
 
 
-MARCH = 10  # tile id of the first marching-solve shape (11 x 3 x 2)
+MARCH = 10  # tile id of the first marching-solve shape (11 marching warps, 6 rows in flight)
 
 
 @pytest.mark.parametrize("tile", range(1, 12))
