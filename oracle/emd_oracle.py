@@ -78,6 +78,11 @@ class Params:
     # with the forced outcome is recorded (trace column 6).  Used to follow the decisions
     # another implementation took at near ties and compare the iterates afterwards.
     force_trials: np.ndarray | None = field(default=None, repr=False)
+    # Storage model (test infrastructure, not part of the method): when True, u and phi are
+    # rounded to binary32 after every accepted iteration, as a solver that keeps its iterates
+    # in single precision does.  Used only to measure how far an instance's answer moves
+    # under that rounding (its conditioning), never as the reference answer.
+    store_f32: bool = False
 
 
 # --------------------------------------------------------------------------- decomposition
@@ -352,6 +357,8 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
         un = math.sqrt(float((nux * nux).sum() + (nut * nut).sum()))
         r_step = du / max(un, 1e-30)
         ux, ut, phi = nux, nut, nphi
+        if p.store_f32:
+            ux, ut, phi = (a.astype(np.float32).astype(np.float64) for a in (ux, ut, phi))
         iters = k + 1
         if record:
             trace.append((alpha, theta, trial, r_feas, r_step, margin, disagree))

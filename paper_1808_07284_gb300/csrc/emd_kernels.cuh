@@ -460,15 +460,16 @@ __device__ void decide(const Ctl &c, State *st, const DecidePrep &d, const doubl
 
 // ------------------------------------------------------------------------------ prepare
 
-// Builds f = Pcal - Pobs in the pitched plane, zeroes or warm-starts the iterates, sums
-// f, f^2, mu, nu and the exact (FP64) differences in FP64 (Sec. 2.1 mass balance) and
-// initialises each gather's state.  Grid: (PX, B); CTA x walks rows x, x + PX, ... of
-// gather blockIdx.y.
+// Builds f = Pcal - Pobs in the pitched plane, zeroes or warm-starts the iterates, sums f,
+// f^2, |Pcal| + |Pobs| and the exact differences Pcal - Pobs in FP64 (Sec. 2.1 mass balance:
+// mu + nu = |Pcal| + |Pobs| and mu - nu = Pcal - Pobs cell by cell, so sum mu and sum nu are
+// half the sum and half the difference of the last two) and initialises each gather's state.
+// Grid: (PX, B); CTA x walks rows x, x + PX, ... of gather blockIdx.y.
 __global__ void __launch_bounds__(kThreads) k_prepare(Ctl c) {
   const int b = blockIdx.y;
   const Shot S = c.shots[b];
   State *st = c.states + b;
-  double sf = 0.0, sf2 = 0.0, smu = 0.0, snu = 0.0, sdx = 0.0;
+  double sf = 0.0, sf2 = 0.0, sab = 0.0, sdx = 0.0;
   for (int i = blockIdx.x; i < S.nr; i += gridDim.x) {
     for (int j = threadIdx.x; j < S.ntp; j += kThreads) {
       const bool in = j < S.nt;
@@ -478,12 +479,11 @@ __global__ void __launch_bounds__(kThreads) k_prepare(Ctl c) {
       const float pp = in ? S.p_pred[g] : 0.0f;
       const float f = pp - po;
       S.f[o] = f;
-      const double fd = static_cast<double>(f);
+      const double fd = static_cast<double>(f), dp = static_cast<double>(pp), dq = static_cast<double>(po);
       sf += fd;
-      sf2 += fd * fd;
-      sdx += static_cast<double>(pp) - static_cast<double>(po);
-      smu += static_cast<double>(fmaxf(pp, 0.0f)) + static_cast<double>(fmaxf(-po, 0.0f));
-      snu += static_cast<double>(fmaxf(po, 0.0f)) + static_cast<double>(fmaxf(-pp, 0.0f));
+      sf2 = fma(fd, fd, sf2);
+      sdx += dp - dq;
+      sab += fabs(dp) + fabs(dq);
       float ux = 0.0f, ut = 0.0f, ph = 0.0f;
       if (in && S.m_init) {
         // the outer faces (x plane row 0, t plane column 0) carry no flux
@@ -501,33 +501,33 @@ __global__ void __launch_bounds__(kThreads) k_prepare(Ctl c) {
     }
   }
   // block reduction in FP64 (this kernel runs once per solve)
-  __shared__ double red[kThreads / 32][5];
+  __shared__ double red[kThreads / 32][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double v[5] = {sf, sf2, smu, snu, sdx};
+  double v[4] = {sf, sf2, sab, sdx};
 #pragma unroll
-  for (int n = 0; n < 5; ++n) {
+  for (int n = 0; n < 4; ++n) {
     v[n] = warp_sum_d(v[n]);
     if (lane == 0) red[warp][n] = v[n];
   }
   __syncthreads();
   double *acc = acc_of(c, b);
-  if (threadIdx.x < 5) {
+  if (threadIdx.x < 4) {
     double t = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
     atomicAdd(acc + (blockIdx.x % kSpread) * kAcc + threadIdx.x, t);
   }
   if (!last_block(&st->ticket, gridDim.x)) return;
-  double a_[5];
-  gather_totals<5>(acc, a_);
+  double a_[4];
+  gather_totals<4>(acc, a_);
   if (threadIdx.x != 0) return;
   const double N = static_cast<double>(S.nr) * S.nt;
   const double fmean = c.balance ? a_[0] / N : 0.0;
   st->fmean = fmean;
   st->fmean_f = static_cast<float>(fmean);
   st->fnorm = sqrt(fmax(a_[1] - 2.0 * fmean * a_[0] + N * fmean * fmean, 0.0));
-  st->mass_mu = S.area * a_[2];
-  st->mass_nu = S.area * a_[3];
-  st->imbalance = S.area * a_[4];
+  st->mass_mu = S.area * 0.5 * (a_[2] + a_[3]);
+  st->mass_nu = S.area * 0.5 * (a_[2] - a_[3]);
+  st->imbalance = S.area * a_[3];
   double alpha;
   if (c.linesearch) {
     alpha = c.alpha0 > 0.0 ? c.alpha0 : 1.0 / sqrt(c.delta * S.lambda);

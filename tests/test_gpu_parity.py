@@ -3,7 +3,9 @@
 Tolerances: dist within 1e-4 relative and phi within 1e-3 relative L2 after the same
 number of accepted iterations; u within 1e-3 relative L2; trial counts equal.  The GPU
 iterates are FP32 (rounding 6e-8 per step) and its inner products FP32 within a warp,
-FP64 above; the oracle is FP64 throughout.
+FP64 above; the oracle is FP64 throughout.  On few-cell grids, whose answer moves by
+more than 1e-4 under binary32 storage alone, the dist tolerance comes from that
+measured change (storage_rtol).
 """
 
 import math
@@ -54,7 +56,7 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def assert_parity(g, r, trials=True, exact_trials=False):
+def assert_parity(g, r, trials=True, exact_trials=False, dist_rtol=DIST_RTOL):
     """Same accepted iterations; the same linesearch trials (up to a rare near-tie decision
     unless exact_trials: the GPU tests the ratio of two FP64 sums of FP32 products, the
     oracle of FP64 norms); then dist, phi and u within the stated tolerances."""
@@ -64,12 +66,27 @@ def assert_parity(g, r, trials=True, exact_trials=False):
         assert g["info"]["ls_trials"] == r["trials"]
     elif trials:
         assert abs(g["info"]["ls_trials"] - r["trials"]) <= max(2, r["trials"] // 1000)
-    assert g["dist"] == pytest.approx(r["dist"], rel=DIST_RTOL)
-    assert g["info"]["dist_l1"] == pytest.approx(r["dist_l1"], rel=DIST_RTOL)
+    assert g["dist"] == pytest.approx(r["dist"], rel=dist_rtol)
+    assert g["info"]["dist_l1"] == pytest.approx(r["dist_l1"], rel=dist_rtol)
     assert rel_l2(g["phi"], r["phi"]) <= PHI_RTOL
     u_g = np.concatenate([g["ux"].ravel(), g["ut"].ravel()])
     u_r = np.concatenate([r["ux"].ravel(), r["ut"].ravel()])
     assert rel_l2(u_g, u_r) <= PHI_RTOL
+
+
+def storage_rtol(r, obs, pred, dt, dx, **kw):
+    """Distance tolerance of an instance from its own conditioning: the oracle is rerun with
+    its iterates rounded to binary32 after every iteration (the GPU's storage precision) and
+    the relative change of dist measured.  On a few-cell gather with the lateral flux still
+    shut (dx = 10 m against dt = 2 ms), phi climbs as the dual ascent on the imbalance
+    between receivers to O(1) while its time differences, which set u, stay near 1e-3, so
+    that rounding alone moves dist by 2e-4 - 3e-4; on gathers of more than a few dozen cells
+    by about 1e-8.  The GPU rounds at more points of a pass than the model (w, div w and
+    the dual update besides the stored iterates), each a perturbation of the same size: it
+    is allowed four times the model's change, and never less than DIST_RTOL."""
+    r32 = O.pdhg(obs, pred, dt, dx, store_f32=True, **kw)
+    assert r32["iters"] == r["iters"] and r32["trials"] == r["trials"]
+    return max(DIST_RTOL, 4.0 * abs(r32["dist"] - r["dist"]) / r["dist"])
 
 
 NEAR_TIE = 1e-3  # relative gap |lhs - rhs| / rhs of a linesearch test that counts as a tie
@@ -174,7 +191,7 @@ def test_ragged_shapes(pkg, nr, nt, tile):
     pred += 0.05 * rng.standard_normal(pred.shape).astype(np.float32)
     r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150)
     g = gpu_solve(pkg, obs, pred, 2e-3, 10.0, max_iter=150, tile=tile)
-    assert_parity(g, r)
+    assert_parity(g, r, dist_rtol=storage_rtol(r, obs, pred, 2e-3, 10.0, max_iter=150))
     if tile:
         assert g["info"]["tile"] == tile
 

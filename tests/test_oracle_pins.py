@@ -374,3 +374,25 @@ def test_forced_trials_replay_is_bit_identical():
     th_prev = tr[k - 1, 1] if k > 0 else 1.0
     assert st[k, 0] == pytest.approx(a_prev * math.sqrt(1.0 + th_prev) * 0.5, rel=1e-14)
     assert not np.array_equal(s["phi"], r["phi"])
+
+
+def test_binary32_storage_model():
+    """store_f32 only rounds the kept iterates: every returned entry is a binary32 value,
+    the default run is untouched, and on a gather of a few thousand cells the distance
+    moves by rounding's size (well under 1e-6), while on a 2 x 2 grid with the lateral flux
+    shut it moves by more than 1e-5 (phi of O(1) against time differences near 1e-3)."""
+    obs, pred = synth.gather_pair_hyperbolic(nt=96, nr=24, dt=2e-3)
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150)
+    q = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150, store_f32=True)
+    for key in ("phi", "ux", "ut"):
+        np.testing.assert_array_equal(q[key], q[key].astype(np.float32).astype(np.float64))
+    assert not np.array_equal(r["phi"], r["phi"].astype(np.float32).astype(np.float64))
+    assert q["trials"] == r["trials"]
+    assert abs(q["dist"] - r["dist"]) <= 1e-6 * r["dist"]
+    rng = np.random.default_rng(2002)
+    obs, pred = synth.gather_pair_hyperbolic(nt=8, nr=2, dt=2e-3, seed=4)
+    obs, pred = obs[:, :2].copy(), pred[:, :2].copy()
+    pred += 0.05 * rng.standard_normal(pred.shape).astype(np.float32)
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150)
+    q = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150, store_f32=True)
+    assert np.all(r["ux"] == 0.0) and abs(q["dist"] - r["dist"]) > 1e-5 * r["dist"]
