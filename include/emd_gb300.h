@@ -224,6 +224,43 @@ emd_status emd_adjoint_batched(int B, const float *const *phi, const int *nt, co
                                float *const *grad_obs, void *workspace, size_t ws_bytes,
                                emd_stream_t stream);
 
+/* Bytes of workspace for emd_misfit_batched_host over B gathers of sizes nt[b] x nr[b]
+ * (host arrays): the batched solve's and the batched adjoint's workspaces, then device
+ * staging for each gather's inputs, phi and m.  0 if any size is invalid. */
+size_t emd_misfit_batched_host_workspace_size(int B, const int *nt, const int *nr);
+
+/*
+ * The misfit step of a full-waveform inversion for gathers held in HOST memory: the B
+ * distances (Sec. 2.1-2.2, Algorithm 1; as emd_dyn_solve_batched) and their adjoint
+ * sources d dist_b / d Pcal_b (Sec. 2.3; as emd_adjoint_batched with params->balance and
+ * upstream gradient 1), host buffers in and out.
+ *  - f_obs, f_pred: HOST arrays of B HOST pointers, each [nr[b]][nt[b]] FP32 row-major.
+ *  - grad_pred: HOST array of B HOST pointers that receive the adjoint sources (same
+ *    layout), or NULL for the distances only; entries may be NULL.
+ *  - nt, nr, dt, dx, results: HOST arrays of B.  params as for emd_dyn_solve_batched; the
+ *    warm-start pointers must be NULL (trace, if set, is a device array as documented).
+ *  - workspace: emd_misfit_batched_host_workspace_size(B, nt, nr) bytes, device, 256-byte
+ *    aligned; phi and m of the solve are kept there and not returned.
+ * The inputs are copied into the workspace gather by gather on a stream the call creates
+ * (ordered after the caller's earlier work on `stream`); each gather's preparation (f, the
+ * mass sums, zeroed iterates) is launched on `stream` behind an event on its own copy, so
+ * it overlaps the copies still in flight.  One batched solve, one batched adjoint and the
+ * copies of the adjoint sources back to grad_pred follow on `stream`, which the call
+ * synchronises: on return the host buffers hold the results.  Page-locked host memory
+ * (cudaHostAlloc, cudaHostRegister) gives the copies the host link's full rate and the
+ * overlap; pageable memory also works, staged by the CUDA driver.  The call allocates no
+ * device memory; it creates and destroys one stream and B + 1 events.
+ * Returns as emd_dyn_solve_batched (adjoint sources are still computed for gathers with a
+ * non-OK status); EMD_ERR_ARG, without copying or launching anything, for an invalid
+ * argument, B > 65535 included; EMD_ERR_WORKSPACE for a NULL, short or misaligned
+ * workspace.
+ */
+emd_status emd_misfit_batched_host(int B, const float *const *f_obs, const float *const *f_pred,
+                                   const int *nt, const int *nr, const double *dt,
+                                   const double *dx, const emd_params *params,
+                                   float *const *grad_pred, emd_result *results, void *workspace,
+                                   size_t ws_bytes, emd_stream_t stream);
+
 /*
  * emd_dyn_solve without a workspace argument, for callers that cannot allocate device
  * memory: code whose host framework owns every device allocation (a custom allocator or

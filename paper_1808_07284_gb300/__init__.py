@@ -20,7 +20,8 @@ from ._binding import (  # noqa: F401
     emd_batched_adjoint_workspace_size, emd_batched_mg_workspace_size,
     emd_batched_workspace_size, emd_decompose, emd_default_mg_params, emd_default_params,
     emd_dyn_solve, emd_dyn_solve_batched, emd_dyn_solve_batched_mg, emd_dyn_solve_mg,
-    emd_dyn_solve_noalloc, emd_lsd, emd_mg_workspace_size, emd_prolong_time, emd_restrict_time,
+    emd_dyn_solve_noalloc, emd_lsd, emd_mg_workspace_size, emd_misfit_batched_host,
+    emd_misfit_batched_host_workspace_size, emd_prolong_time, emd_restrict_time,
     emd_status_string, emd_tile_count, emd_workspace_size, lib, new_workspace,
 )
 
@@ -30,7 +31,8 @@ __all__ = [
     "emd_batched_workspace_size", "emd_status_string", "emd_tile_count", "EmdError",
     "emd_dyn_solve_mg", "emd_dyn_solve_batched_mg", "emd_default_mg_params", "emd_mg_workspace_size",
     "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time", "emd_lsd", "lsd_loss",
-    "LSDFunction", "emd_adjoint_batched", "emd_batched_adjoint_workspace_size",
+    "LSDFunction", "emd_adjoint_batched", "emd_batched_adjoint_workspace_size", "emd_misfit_host",
+    "emd_misfit_batched_host", "emd_misfit_batched_host_workspace_size",
 ]
 
 
@@ -90,6 +92,29 @@ def emd_batched(f_obs, f_pred, dts, dxs, workspace=None, stream=None, check=True
         emd_batched_workspace_size(nts, nrs), f_obs[0].device)
     res = emd_dyn_solve_batched(f_obs, f_pred, dts, dxs, p, phis, ms, ws, stream, check=check)
     return [r.dist for r in res], phis, ms, [r.as_dict() for r in res]
+
+
+def emd_misfit_host(f_obs, f_pred, dts, dxs, grad_preds=None, adjoint=True, workspace=None,
+                    device=None, stream=None, check=True, **params):
+    """Distances and adjoint sources of B gathers held in host memory, in one call of the C
+    ABI (``emd_misfit_batched_host``): lists of CPU float32 tensors in (page-locked for the
+    host link's full rate), ``(dists, grad_preds, infos)`` out.  ``grad_preds``: CPU tensors
+    to receive the adjoint sources (allocated page-locked when None and ``adjoint``)."""
+    import torch
+    B = len(f_obs)
+    dts = [float(v) for v in (dts if hasattr(dts, "__len__") else [dts] * B)]
+    dxs = [float(v) for v in (dxs if hasattr(dxs, "__len__") else [dxs] * B)]
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    p = emd_default_params(**params)
+    if adjoint and grad_preds is None:
+        grad_preds = [torch.empty(tuple(t.shape), dtype=torch.float32).pin_memory() for t in f_obs]
+    if not adjoint:
+        grad_preds = None
+    nts, nrs = [int(t.shape[1]) for t in f_obs], [int(t.shape[0]) for t in f_obs]
+    ws = workspace if workspace is not None else new_workspace(
+        emd_misfit_batched_host_workspace_size(nts, nrs), dev)
+    res = emd_misfit_batched_host(f_obs, f_pred, dts, dxs, p, grad_preds, ws, stream, check=check)
+    return [r.dist for r in res], grad_preds, [r.as_dict() for r in res]
 
 
 def _autograd_function():

@@ -24,6 +24,7 @@ EXPORTS = (
     "emd_status_string", "emd_dyn_solve_noalloc", "emd_default_mg_params", "emd_mg_workspace_size",
     "emd_batched_mg_workspace_size", "emd_restrict_time", "emd_prolong_time", "emd_dyn_solve_mg",
     "emd_dyn_solve_batched_mg", "emd_lsd", "emd_batched_adjoint_workspace_size", "emd_adjoint_batched",
+    "emd_misfit_batched_host_workspace_size", "emd_misfit_batched_host",
 )
 
 
@@ -112,6 +113,12 @@ def lib() -> ctypes.CDLL:
                                           P(c_double), c_int, c_void_p, P(c_void_p), P(c_void_p),
                                           c_void_p, c_size_t, c_void_p]
         L.emd_adjoint_batched.restype = c_int
+        L.emd_misfit_batched_host_workspace_size.argtypes = [c_int, P(c_int), P(c_int)]
+        L.emd_misfit_batched_host_workspace_size.restype = c_size_t
+        L.emd_misfit_batched_host.argtypes = [c_int, P(c_void_p), P(c_void_p), P(c_int), P(c_int),
+                                              P(c_double), P(c_double), P(EmdParams), P(c_void_p),
+                                              P(EmdResult), c_void_p, c_size_t, c_void_p]
+        L.emd_misfit_batched_host.restype = c_int
         L.emd_dyn_solve_noalloc.argtypes = [c_void_p, c_void_p, c_int, c_int, c_double, c_double,
                                             P(EmdParams), c_void_p, c_void_p, P(EmdResult), c_void_p]
         L.emd_dyn_solve_noalloc.restype = c_int
@@ -314,6 +321,44 @@ def emd_adjoint_batched(phis, dts, dxs, balance, grad_out, grad_preds, grad_obss
                                    workspace.numel(), _stream(stream))
     if st != EMD_OK:
         raise EmdError(st, "emd_adjoint_batched")
+
+
+def emd_misfit_batched_host_workspace_size(nts, nrs) -> int:
+    B = len(nts)
+    return lib().emd_misfit_batched_host_workspace_size(B, (c_int * B)(*nts), (c_int * B)(*nrs))
+
+
+def _check_host_grid(t, nr, nt, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CPU tensor")
+    if t.numel() != nr * nt:
+        raise ValueError(f"{name} must hold {nr} x {nt} elements, got {t.numel()}")
+
+
+def emd_misfit_batched_host(f_obs, f_pred, dts, dxs, params: EmdParams, grad_preds, workspace,
+                            stream=None, check: bool = True):
+    """Distances and adjoint sources of B gathers held in host memory (CPU tensors, pinned
+    for full speed); grad_preds: list of CPU tensors (entries may be None) or None.
+    Returns a list of EmdResult."""
+    B = len(f_obs)
+    nts, nrs = [int(t.shape[1]) for t in f_obs], [int(t.shape[0]) for t in f_obs]
+    for b in range(B):
+        _check_host_grid(f_obs[b], nrs[b], nts[b], f"f_obs[{b}]")
+        _check_host_grid(f_pred[b], nrs[b], nts[b], f"f_pred[{b}]")
+        if grad_preds is not None and grad_preds[b] is not None:
+            _check_host_grid(grad_preds[b], nrs[b], nts[b], f"grad_pred[{b}]")
+    P = c_void_p * B
+    gp = None if grad_preds is None else P(*[_ptr(t) for t in grad_preds])
+    res = (EmdResult * B)()
+    st = lib().emd_misfit_batched_host(
+        B, P(*[_ptr(t) for t in f_obs]), P(*[_ptr(t) for t in f_pred]), (c_int * B)(*nts),
+        (c_int * B)(*nrs), (c_double * B)(*dts), (c_double * B)(*dxs), ctypes.byref(params), gp,
+        res, _ptr(workspace), workspace.numel(), _stream(stream))
+    if check and st != EMD_OK:
+        raise EmdError(st, "emd_misfit_batched_host")
+    return list(res)
 
 
 def emd_dyn_solve_noalloc(f_obs, f_pred, dt, dx, params: EmdParams, phi, m, stream=None,

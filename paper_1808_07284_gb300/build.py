@@ -16,12 +16,8 @@ ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libemd_gb300.so")
 SOURCES = [os.path.join(HERE, "csrc", "emd_api.cu"), os.path.join(HERE, "csrc", "emd_noalloc.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "emd_kernels.cuh"),
-                  os.path.join(HERE, "csrc", "emd_lsd.cuh"),
-                  os.path.join(HERE, "csrc", "emd_multigrid.cuh"),
-                  os.path.join(HERE, "csrc", "emd_pass_tma.cuh"),
-                  os.path.join(HERE, "csrc", "emd_resident.cuh"),
-                  os.path.join(ROOT, "include", "emd_gb300.h")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", n) for n in sorted(os.listdir(os.path.join(HERE, "csrc")))
+                  if n.endswith(".cuh")] + [os.path.join(ROOT, "include", "emd_gb300.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -355,6 +356,16 @@ struct SolveExtra {
   bool finalize = true;
   bool no_tune = false;   // tile 0 takes the untuned default shape (no timed trial solves)
   bool no_graph = false;  // per-pass fallback by plain launches (capturing a graph allocates)
+  // ready[b]: recorded (on another stream) once gather b's inputs are in place.  Each
+  // gather is then prepared by a launch of its own after waiting on its event, so the
+  // preparation of the first gathers overlaps the copies of the later ones.
+  const cudaEvent_t *ready = nullptr;
+  // Enqueues the copies that `ready` waits on.  The first solve to reach its prepares (the
+  // solve itself, or the autotuner's first trial) runs it once and clears it: the copies
+  // are queued after that solve's small host tables, which are pageable copies -- queued
+  // behind gigabytes of copies they would hold the host thread until those had finished,
+  // and the prepares would be enqueued only after the copies instead of beside them.
+  std::function<emd_status()> *stage = nullptr;
 };
 
 emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pred, const int *nt,
@@ -555,10 +566,24 @@ emd_status solve_impl(int B, const float *const *f_obs, const float *const *f_pr
   EMD_CK(cudaFuncSetAttribute(sh.fin, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(smem)));
 
-  emd::k_prepare<<<dim3(std::min(nr_max, 128), B), kThreads, 0, stream>>>(ctl);
-  EMD_CK(cudaGetLastError());
+  if (x.stage && *x.stage) {
+    const std::function<emd_status()> enqueue = std::move(*x.stage);
+    *x.stage = nullptr;
+    const emd_status s = enqueue();
+    if (s != EMD_OK) return s;
+  }
+  if (x.ready) {
+    for (int b = 0; b < B; ++b) {
+      EMD_CK(cudaStreamWaitEvent(stream, x.ready[b], 0));
+      emd::k_prepare<<<dim3(std::min(nr[b], 128), 1), kThreads, 0, stream>>>(ctl, b);
+      EMD_CK(cudaGetLastError());
+    }
+  } else {
+    emd::k_prepare<<<dim3(std::min(nr_max, 128), B), kThreads, 0, stream>>>(ctl, 0);
+    EMD_CK(cudaGetLastError());
+  }
 
-  int n_launch = 1;  // k_prepare
+  int n_launch = x.ready ? B : 1;  // k_prepare
   if (resident) {
     const size_t rsmem = emd::resident_smem_bytes(max_cells);
     EMD_CK(cudaFuncSetAttribute(emd::k_solve_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1053,6 +1078,110 @@ emd_status emd_adjoint_batched(int B, const float *const *phi, const int *nt, co
   emd::k_adj_scale_batched<<<dim3(bx, B), kThreads, 0, stream>>>(djobs, acc, balance);
   EMD_CK(cudaGetLastError());
   return EMD_OK;
+}
+
+size_t emd_misfit_batched_host_workspace_size(int B, const int *nt, const int *nr) {
+  const size_t solve = emd_batched_workspace_size(B, nt, nr);
+  if (solve == 0) return 0;
+  size_t t = align256(solve) + align256(emd_batched_adjoint_workspace_size(B));
+  for (int b = 0; b < B; ++b) {
+    const size_t plane = sizeof(float) * static_cast<size_t>(nt[b]) * nr[b];
+    t += 3 * align256(plane) + align256(2 * plane);  // obs (then the adjoint source), pred, phi; m
+  }
+  return t;
+}
+
+emd_status emd_misfit_batched_host(int B, const float *const *f_obs, const float *const *f_pred,
+                                   const int *nt, const int *nr, const double *dt,
+                                   const double *dx, const emd_params *params,
+                                   float *const *grad_pred, emd_result *results, void *workspace,
+                                   size_t ws_bytes, emd_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  emd_params p;
+  emd_default_params(&p);
+  if (params) p = *params;
+  if (B < 1 || B > 65535 || !f_obs || !f_pred || !nt || !nr || !dt || !dx || !results)
+    return EMD_ERR_ARG;
+  if (!params_ok(p) || p.phi_init || p.m_init) return EMD_ERR_ARG;
+  for (int b = 0; b < B; ++b) {
+    if (!f_obs[b] || !f_pred[b] || !size_ok(nt[b], nr[b])) return EMD_ERR_ARG;
+    if (!(dt[b] > 0) || !std::isfinite(dt[b]) || !(dx[b] > 0) || !std::isfinite(dx[b]))
+      return EMD_ERR_ARG;
+  }
+  const size_t need = emd_misfit_batched_host_workspace_size(B, nt, nr);
+  if (!workspace || !aligned256(workspace) || ws_bytes < need) return EMD_ERR_WORKSPACE;
+
+  // workspace: the solve's, the adjoint's, then per gather obs | pred | phi | m
+  const size_t solve_ws = emd_batched_workspace_size(B, nt, nr);
+  const size_t adj_ws = emd_batched_adjoint_workspace_size(B);
+  char *base = static_cast<char *>(workspace);
+  char *q = base + align256(solve_ws) + align256(adj_ws);
+  std::vector<const float *> d_obs(B), d_pred(B);
+  std::vector<float *> d_gp(B), d_phi(B), d_m(B);
+  std::vector<size_t> bytes(B);
+  for (int b = 0; b < B; ++b) {
+    bytes[b] = sizeof(float) * static_cast<size_t>(nt[b]) * nr[b];
+    d_gp[b] = reinterpret_cast<float *>(q);  // the adjoint source reuses the obs staging
+    d_obs[b] = d_gp[b];
+    q += align256(bytes[b]);
+    d_pred[b] = reinterpret_cast<const float *>(q);
+    q += align256(bytes[b]);
+    d_phi[b] = reinterpret_cast<float *>(q);
+    q += align256(bytes[b]);
+    d_m[b] = reinterpret_cast<float *>(q);
+    q += align256(2 * bytes[b]);
+  }
+
+  // The copies run on a stream of this call, ordered after the caller's earlier work on
+  // `stream`; each gather's event lets its preparation start as soon as it has landed.
+  struct Owned {
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~Owned() {
+      if (cs) {
+        (void)cudaStreamSynchronize(cs);  // no copy may still write the workspace on return
+        (void)cudaStreamDestroy(cs);
+      }
+      for (cudaEvent_t e : ev) (void)cudaEventDestroy(e);
+    }
+  } own;
+  EMD_CK(cudaStreamCreateWithFlags(&own.cs, cudaStreamNonBlocking));
+  own.ev.reserve(B + 1);
+  for (int i = 0; i <= B; ++i) {
+    cudaEvent_t e;
+    EMD_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    own.ev.push_back(e);
+  }
+  EMD_CK(cudaEventRecord(own.ev[B], stream));
+  EMD_CK(cudaStreamWaitEvent(own.cs, own.ev[B], 0));
+  std::function<emd_status()> stage = [&]() -> emd_status {
+    for (int b = 0; b < B; ++b) {
+      EMD_CK(cudaMemcpyAsync(d_gp[b], f_obs[b], bytes[b], cudaMemcpyHostToDevice, own.cs));
+      EMD_CK(cudaMemcpyAsync(const_cast<float *>(d_pred[b]), f_pred[b], bytes[b],
+                             cudaMemcpyHostToDevice, own.cs));
+      EMD_CK(cudaEventRecord(own.ev[b], own.cs));
+    }
+    return EMD_OK;
+  };
+
+  SolveExtra x;
+  x.ready = own.ev.data();
+  x.stage = &stage;
+  const emd_status st = solve_impl(B, d_obs.data(), d_pred.data(), nt, nr, dt, dx, &p, d_phi.data(),
+                                   d_m.data(), results, base, solve_ws, stream, x);
+  if (st == EMD_ERR_ARG || st == EMD_ERR_CUDA || st == EMD_ERR_TIMEOUT || st == EMD_ERR_WORKSPACE)
+    return st;
+  if (grad_pred) {
+    const emd_status sa = emd_adjoint_batched(B, d_phi.data(), nt, nr, dt, dx, p.balance, nullptr,
+                                              d_gp.data(), nullptr, base + align256(solve_ws),
+                                              adj_ws, stream_);
+    if (sa != EMD_OK) return sa;
+    for (int b = 0; b < B; ++b)
+      if (grad_pred[b])
+        EMD_CK(cudaMemcpyAsync(grad_pred[b], d_gp[b], bytes[b], cudaMemcpyDeviceToHost, stream));
+    EMD_CK(cudaStreamSynchronize(stream));
+  }
+  return st;
 }
 
 void emd_default_mg_params(emd_mg_params *p) {

@@ -464,9 +464,9 @@ __device__ void decide(const Ctl &c, State *st, const DecidePrep &d, const doubl
 // f^2, |Pcal| + |Pobs| and the exact differences Pcal - Pobs in FP64 (Sec. 2.1 mass balance:
 // mu + nu = |Pcal| + |Pobs| and mu - nu = Pcal - Pobs cell by cell, so sum mu and sum nu are
 // half the sum and half the difference of the last two) and initialises each gather's state.
-// Grid: (PX, B); CTA x walks rows x, x + PX, ... of gather blockIdx.y.
-__global__ void __launch_bounds__(kThreads) k_prepare(Ctl c) {
-  const int b = blockIdx.y;
+// Grid: (PX, n); CTA x walks rows x, x + PX, ... of gather b0 + blockIdx.y.
+__global__ void __launch_bounds__(kThreads) k_prepare(Ctl c, int b0) {
+  const int b = b0 + static_cast<int>(blockIdx.y);
   const Shot S = c.shots[b];
   State *st = c.states + b;
   double sf = 0.0, sf2 = 0.0, sab = 0.0, sdx = 0.0;

@@ -198,3 +198,48 @@ def test_batched_adjoint_argument_errors_need_no_gpu(B):
     assert call(n=nbytes - 8) == B.EMD_ERR_WORKSPACE
     assert call(ws=ctypes.c_void_p(264)) == B.EMD_ERR_WORKSPACE
     assert call(ws=None) == B.EMD_ERR_WORKSPACE
+
+
+def test_host_misfit_argument_errors_need_no_gpu(B):
+    """emd_misfit_batched_host sizes its workspace as the solve's plus the adjoint's plus the
+    staging of each gather, and refuses bad sizes, spacings, parameters, warm starts, null
+    pointers, B > 65535 and a short or misaligned workspace before any CUDA call."""
+    L = B.lib()
+    P2, I2, D2 = ctypes.c_void_p * 2, ctypes.c_int * 2, ctypes.c_double * 2
+    nts, nrs = (8, 300), (4, 7)
+    nbytes = B.emd_misfit_batched_host_workspace_size(list(nts), list(nrs))
+
+    def a256(n):
+        return (n + 255) // 256 * 256
+
+    staging = sum(3 * a256(4 * t * r) + a256(8 * t * r) for t, r in zip(nts, nrs))
+    assert nbytes == (a256(B.emd_batched_workspace_size(list(nts), list(nrs)))
+                      + a256(B.emd_batched_adjoint_workspace_size(2)) + staging)
+    assert B.emd_misfit_batched_host_workspace_size([8, 1], [4, 4]) == 0
+    host = [(ctypes.c_float * (t * r))() for t, r in zip(nts, nrs)]
+    ptrs = P2(*[ctypes.addressof(h) for h in host])
+    res = (B.EmdResult * 2)()
+    fake = ctypes.c_void_p(256)
+
+    def call(Bn=2, obs=ptrs, pred=ptrs, nt=nts, nr=nrs, dt=(1e-3, 1e-3), dx=(10.0, 10.0), prm=None,
+             ws=fake, n=nbytes, results=res):
+        p = B.emd_default_params()
+        for k, v in (prm or {}).items():
+            setattr(p, k, v)
+        return L.emd_misfit_batched_host(Bn, obs, pred, I2(*nt), I2(*nr), D2(*dt), D2(*dx), ctypes.byref(p),
+                                         None, results, ws, n, None)
+
+    assert call(Bn=0) == B.EMD_ERR_ARG
+    assert call(Bn=65536) == B.EMD_ERR_ARG
+    assert call(obs=P2(ptrs[0], None)) == B.EMD_ERR_ARG
+    assert call(pred=None) == B.EMD_ERR_ARG
+    assert call(results=None) == B.EMD_ERR_ARG
+    assert call(nt=(8, 1)) == B.EMD_ERR_ARG
+    assert call(dt=(1e-3, 0.0)) == B.EMD_ERR_ARG
+    assert call(dx=(float("inf"), 10.0)) == B.EMD_ERR_ARG
+    assert call(prm=dict(xi=1.5)) == B.EMD_ERR_ARG
+    assert call(prm=dict(max_iter=0)) == B.EMD_ERR_ARG
+    assert call(prm=dict(phi_init=256)) == B.EMD_ERR_ARG
+    assert call(n=nbytes - 8) == B.EMD_ERR_WORKSPACE
+    assert call(ws=ctypes.c_void_p(264)) == B.EMD_ERR_WORKSPACE
+    assert call(ws=None) == B.EMD_ERR_WORKSPACE
