@@ -269,14 +269,25 @@ __device__ __forceinline__ void march_unit(const MarchUnit &m, float *ring, floa
 
   // rows whose r, r - 1, r - 2 lie in the gather with r - 2 > 0 and an owned r - 2
   const int fast_lo = max(4, 5 - m.i0), fast_hi = min(m.h + 2, nr - m.i0 + 1);
+  // Fast rows go two per trip, so the values carried from one row to the next change
+  // registers between the two steps instead of being copied back after every row.
+  int r = 0;
 #pragma unroll 1
-  for (int r = 0; r < nrows; ++r) {
-    cp_async_wait<D - 1>();  // row r's group has landed (later rows may still be in flight)
-    if (r >= fast_lo && r <= fast_hi)
+  while (r < nrows) {
+    if (r >= fast_lo && r + 1 <= fast_hi) {
+      cp_async_wait<D - 1>();  // row r's group has landed (later rows may still be in flight)
       row_step(r, BoolConst<true>{});
-    else
+      march_issue<D>(m, r + D, ring);  // row r's ring row is free: stage row r + D into it
+      cp_async_wait<D - 1>();
+      row_step(r + 1, BoolConst<true>{});
+      march_issue<D>(m, r + 1 + D, ring);
+      r += 2;
+    } else {
+      cp_async_wait<D - 1>();
       row_step(r, BoolConst<false>{});
-    march_issue<D>(m, r + D, ring);  // row r's ring row is free: stage row r + D into it
+      march_issue<D>(m, r + D, ring);
+      r += 1;
+    }
   }
   march_fold(v, mine);
 }
