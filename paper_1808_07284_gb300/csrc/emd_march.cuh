@@ -203,8 +203,8 @@ __device__ __forceinline__ void march_unit(const MarchUnit &m, float *ring, floa
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               if (!cin[q]) continue;
-              v[7] += nx[q] * nx[q] + nv[q] * nv[q];
-              v[8] += ddx[q] * ddx[q] + ddt[q] * ddt[q];
+              v[7] = fmaf(nx[q], nx[q], fmaf(nv[q], nv[q], v[7]));
+              v[8] = fmaf(ddx[q], ddx[q], fmaf(ddt[q], ddt[q], v[8]));
             }
           }
         }
@@ -242,9 +242,9 @@ __device__ __forceinline__ void march_unit(const MarchUnit &m, float *ring, floa
               v[0] = fmaf(pc[q], pc[q], v[0]);
               v[1] = fmaf(pc[q], qc[q], v[1]);
               v[2] = fmaf(qc[q], qc[q], v[2]);
-              v[3] += gpx * gpx + gpt * gpt;
-              v[4] += gpx * gqx + gpt * gqt;
-              v[5] += gqx * gqx + gqt * gqt;
+              v[3] = fmaf(gpx, gpx, fmaf(gpt, gpt, v[3]));
+              v[4] = fmaf(gpx, gqx, fmaf(gpt, gqt, v[4]));
+              v[5] = fmaf(gqx, gqx, fmaf(gqt, gqt, v[5]));
             }
           }
           if (++folded == kFoldRows) {
