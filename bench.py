@@ -484,6 +484,10 @@ def run_marine(a):
                 extras["marine_one_by_one"] = _marine_single_extra(P, obs, pred, phis, ms, stream)
                 extras["transmissive_3000x400"] = _transmissive_extra(P, dev, stream, a)
                 extras["uneven48_200_iterations"] = _uneven48_extra(P, dev, a)
+                if not a.no_cpu_baseline:
+                    tr = extras["transmissive_3000x400"]
+                    extras["cpu_baseline_small_configs"] = _small_configs_cpu_extra(
+                        P, dev, stream, cores, tr["ms_per_solve"] / 1e3 / tr["iters"])
             extras["clocks_extras"] = clk_x.summary()
         if pending is not None:
             pool, jobs = pending
@@ -623,6 +627,79 @@ def _transmissive_extra(P, dev, stream, a):
                          "dist": fr.dist},
             "note": "L2-resident (43 MB of state): bound by the per-pass chain, not HBM; residual 1e-5 is "
                     "out of reach in physical units (FP64 included), so 1e-2"}
+
+
+def _oracle_shift(args):
+    """The oracle on one shift of the 1D sweep (a worker of a spawned pool): (dist, seconds)."""
+    dt, obs, pred, iters = args
+    from oracle import emd_oracle as O
+    t = time.perf_counter()
+    r = O.pdhg(obs, pred, dt, 1.0, max_iter=iters)
+    return r["dist"], time.perf_counter() - t
+
+
+def _small_configs_cpu_extra(P, dev, stream, cores, t_iter_3000x400):
+    """The oracle at the GPU's iteration count on the small configurations, next to the GPU's
+    time for the same work: the 256 x 64 gather (2000 iterations, one core), the 1D sweep of
+    61 shifts of a 1024-sample Ricker pair (2000 iterations each, one process per core), and
+    a 20-iteration sample of the 3000 x 400 gather (per iteration, one core)."""
+    import torch
+    import synth
+    from oracle import emd_oracle as O
+    K = 2000
+
+    def gpu_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    out = {}
+    obs, pred = synth.gather_pair_hyperbolic()
+    nr, nt = obs.shape
+    o, p = torch.from_numpy(obs).to(dev), torch.from_numpy(pred).to(dev)
+    ws = P.new_workspace(P.emd_workspace_size(nt, nr), dev)
+    phi = torch.empty((nr, nt), dtype=torch.float32, device=dev)
+    m = torch.empty((2, nr, nt), dtype=torch.float32, device=dev)
+    prm = P.emd_default_params(max_iter=K)
+    g_ms, r = gpu_ms(lambda: P.emd_dyn_solve(o, p, 2e-3, 10.0, prm, phi, m, ws, stream))
+    t = time.perf_counter()
+    ro = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=K)
+    o_s = time.perf_counter() - t
+    out["hyperbolic_256x64_2000_iterations"] = {
+        "gpu_ms": g_ms, "oracle_s": o_s, "oracle_cores": 1,
+        "gpu_cell_updates_per_s": nr * nt * K / (g_ms / 1e3), "oracle_cell_updates_per_s": nr * nt * K / o_s,
+        "dist_rel": abs(r.dist - ro["dist"]) / ro["dist"], "gpu_tile": r.tile}
+
+    dt, obs1, preds = synth.shift_sweep_1d(nt=1024)
+    O_ = [torch.from_numpy(obs1).to(dev)] * len(preds)
+    P_ = [torch.from_numpy(q).to(dev) for _, q in preds]
+    g_ms, (dists, _phis, _ms, _infos) = gpu_ms(lambda: P.emd_batched(O_, P_, dt, 1.0, max_iter=K))
+    n_proc = max(1, min(16, cores))
+    with mp.get_context("spawn").Pool(n_proc) as pool:
+        pool.map(_oracle_shift, [(dt, obs1, preds[0][1], 10)] * n_proc)  # workers' imports
+        t = time.perf_counter()
+        res = pool.map(_oracle_shift, [(dt, obs1, q, K) for _, q in preds])
+        o_s = time.perf_counter() - t
+    rel = [abs(d - ro_) / ro_ for d, (ro_, _) in zip(dists, res) if ro_ > 0]
+    out["shift_sweep_1d_61x1024_2000_iterations"] = {
+        "gpu_ms": g_ms, "oracle_s": o_s, "oracle_cores": n_proc,
+        "oracle_cpu_s": sum(s_ for _, s_ in res), "max_dist_rel": max(rel),
+        "note": "the 61 shifts in one batched GPU call (one shared-memory-resident CTA each)"}
+
+    obs2, pred2 = synth.gather_pair_transmissive(nt=NT, nr=NR, dt=DT, dx=DX)
+    n2 = 20
+    t = time.perf_counter()
+    O.pdhg(obs2, pred2, DT, DX, max_iter=n2)
+    o_s = time.perf_counter() - t
+    out["transmissive_3000x400_per_iteration"] = {
+        "gpu_us": 1e6 * t_iter_3000x400, "oracle_ms": 1e3 * o_s / n2, "oracle_cores": 1,
+        "sample": f"{n2} oracle iterations; GPU: the residual-1e-2 solve of transmissive_3000x400 per iteration"}
+    return out
 
 
 def _uneven48_extra(P, dev, a):

@@ -343,6 +343,18 @@ __device__ Decision decide_core(const Ctl &c, const DecidePrep &d, const double 
   if (!finite) {
     o.status = ST_NONFINITE;
     o.done = true;
+  } else if (c.linesearch && Ppp == 0.0 && Pqq == 0.0) {
+    // p and q identically zero (identical gathers, u = 0): the dual move is zero for every
+    // step size and every trial would pass.  The step keeps the lower end alpha_k of
+    // [alpha_k, alpha_k sqrt(1 + theta_k)] (theta = 1); growing by the upper end, it would
+    // overflow the FP32 dual step within about 200 iterations and inf * 0 would turn phi
+    // into NaN (reading Q20).
+    o.theta = 1.0;
+    o.coef = c.delta * o.alpha;
+    o.alpha_f = static_cast<float>(o.alpha);
+    o.coef_f = static_cast<float>(o.coef);
+    o.theta_f = 1.0f;
+    o.inv_f = 1.0f / (1.0f + static_cast<float>(c.eps * o.alpha));
   } else if (c.linesearch) {
     const bool pass0 = lane < c.ls_max_trials && c.debug_fault != 1 &&
                        d.cl * fma(d.s_lane2, Gqq, fma(d.s2x, Gpq, Gpp)) <=

@@ -298,6 +298,37 @@ def test_1d_shift_sweep_matches_closed_form(pkg):
         assert c["info"]["dist_l1"] == pytest.approx(w, rel=1e-3), (s, c["info"])
 
 
+@pytest.mark.parametrize("case,tile", [("1d", 0), ("2d", 0), ("2d", 7), ("2d", MARCH)])
+def test_identical_gathers(pkg, case, tile):
+    """Reading Q20 on every solver path: identical gathers make p and q identically zero, so the
+    step stays at alpha_0 (theta = 1, one trial per iteration) as in the oracle.  After 2500
+    iterations, past the point where a growing step overflows, phi and m are exactly zero and
+    finite, the distance is 0, and the adjoint source is zero."""
+    if case == "1d":
+        dt, obs, _ = synth.shift_sweep_1d(nt=1024, shifts=[0.1])
+        dx = 1.0
+    else:
+        obs, _ = synth.gather_pair_hyperbolic()
+        dt, dx = 2e-3, 10.0
+    K = 2500
+    g = gpu_solve(pkg, obs, obs.copy(), dt, dx, max_iter=K, trace=True, tile=tile)
+    r = O.pdhg(obs, obs.copy(), dt, dx, max_iter=K, record=True)
+    info = g["info"]
+    assert info["status"] == 0 and info["iters"] == K and info["ls_trials"] == K == r["trials"]
+    np.testing.assert_allclose(g["trace"][:, 0], r["trace"][:, 0], rtol=1e-15)
+    np.testing.assert_array_equal(g["trace"][:, 1], 1.0)
+    for key in ("phi", "ux", "ut"):
+        assert np.all(g[key] == 0.0), key
+    assert g["dist"] == 0.0 and info["dist_l1"] == 0.0
+    if tile:
+        assert info["tile"] == tile
+    dev = torch.device("cuda:0")
+    o = torch.from_numpy(obs).to(dev)
+    pr = o.clone().requires_grad_(True)
+    pkg.emd_loss(pr, o, dt, dx, max_iter=300).backward()
+    assert torch.all(pr.grad == 0.0)
+
+
 def test_decompose(pkg):
     obs, pred = synth.gather_pair_transmissive(nt=500, nr=40, seed=9)
     dev = torch.device("cuda:0")
@@ -650,6 +681,7 @@ def test_1d_shift_sweep_61_shifts_batched(pkg):
     O_ = [torch.from_numpy(obs).to(dev)] * len(preds)
     P_ = [torch.from_numpy(p).to(dev) for _, p in preds]
     d, phis, ms, infos = pkg.emd_batched(O_, P_, dt, 1.0, max_iter=100000)
+    assert all(bool(torch.isfinite(ph).all()) for ph in phis)  # zero shift included (Q20)
     shifts = np.array([s for s, _ in preds])
     w = []
     for (s, p), info in zip(preds, infos):

@@ -396,3 +396,28 @@ def test_binary32_storage_model():
     r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150)
     q = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150, store_f32=True)
     assert np.all(r["ux"] == 0.0) and abs(q["dist"] - r["dist"]) > 1e-5 * r["dist"]
+
+
+def test_identical_gathers_keep_the_step_and_stay_finite():
+    """Reading Q20: identical gathers (f = 0) make p and q identically zero, so the dual move is
+    zero for every step size.  The step stays at alpha_0 with theta = 1 and one trial per
+    iteration.  phi and u stay exactly zero and finite past the 1,500 iterations after which a
+    step growing by the upper end sqrt(1 + theta) would overflow.  Gathers one ulp apart take
+    the usual upper-end trial (backtracked by xi) from the first iteration."""
+    for obs, dt, dx in [(synth.shift_sweep_1d(nt=256)[1], 1 / 255, 1.0),
+                        (synth.gather_pair_hyperbolic(nt=64, nr=8)[0], 2e-3, 10.0)]:
+        r = O.pdhg(obs, obs.copy(), dt, dx, max_iter=2500, record=True)
+        tr = r["trace"]
+        a0 = 1.0 / math.sqrt(1e5 * O.lambda_bound(obs.shape[0], dt, dx))
+        assert r["status"] == O.STATUS_OK and r["iters"] == 2500 and r["trials"] == 2500
+        np.testing.assert_array_equal(tr[:, 0], a0)
+        np.testing.assert_array_equal(tr[:, 1], 1.0)
+        for key in ("phi", "ux", "ut"):
+            assert np.all(r[key] == 0.0)
+        assert r["dist"] == 0.0
+        near = obs.copy()
+        near.flat[near.size // 2] = np.nextafter(near.flat[near.size // 2], np.float32(np.inf))
+        q = O.pdhg(obs, near, dt, dx, max_iter=3, record=True)
+        t = int(q["trace"][0, 2]) - 1  # backtracking steps of the first iteration
+        assert q["trace"][0, 0] == pytest.approx(a0 * math.sqrt(2.0) * 0.5 ** t, rel=1e-15)
+        assert q["trace"][0, 1] != 1.0
