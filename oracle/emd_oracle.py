@@ -315,14 +315,17 @@ def pdhg(p_obs, p_pred, dt, dx, params: Params | None = None, record: bool = Fal
         nux, nut = primal_step(ux, ut, phi, alpha, p.eps, dt, dx, p.norm)
         disagree = 0.0
         if p.linesearch:
-            # Reading Q20: with p = div u^{k+1} + f and q = div(u^{k+1} - u^k) both identically
-            # zero (identical gathers, u = 0) the dual move beta (p + theta q) is zero for every
-            # step size, so every trial passes.  The step then takes the lower end alpha_k of
-            # [alpha_k, alpha_k sqrt(1 + theta_k)] (theta = 1) rather than growing by about 1.6
-            # per iteration until it overflows and inf * 0 turns phi into NaN.
-            pk = divergence(nux, nut, dt, dx) + f
-            qk = divergence(nux - ux, nut - ut, dt, dx)
-            still = not pk.any() and not qk.any()
+            # Reading Q20: identical gathers (the balanced f identically zero) with p = div u^{k+1}
+            # + f and q = div(u^{k+1} - u^k) both identically zero make the dual move beta (p +
+            # theta q) zero for every step size, so every trial passes on every iteration.  The
+            # step then takes the lower end alpha_k of [alpha_k, alpha_k sqrt(1 + theta_k)]
+            # (theta = 1) rather than growing by about 1.6 per iteration until it overflows and
+            # inf * 0 turns phi into NaN.
+            still = False
+            if fnorm == 0.0:
+                pk = divergence(nux, nut, dt, dx) + f
+                qk = divergence(nux - ux, nut - ut, dt, dx)
+                still = not pk.any() and not qk.any()
             a = alpha if still else alpha * math.sqrt(1.0 + theta)
             accepted = False
             margin = math.inf  # closest any trial of this iteration came to the test's threshold

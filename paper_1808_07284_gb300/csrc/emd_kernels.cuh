@@ -343,12 +343,12 @@ __device__ Decision decide_core(const Ctl &c, const DecidePrep &d, const double 
   if (!finite) {
     o.status = ST_NONFINITE;
     o.done = true;
-  } else if (c.linesearch && Ppp == 0.0 && Pqq == 0.0) {
-    // p and q identically zero (identical gathers, u = 0): the dual move is zero for every
-    // step size and every trial would pass.  The step keeps the lower end alpha_k of
-    // [alpha_k, alpha_k sqrt(1 + theta_k)] (theta = 1); growing by the upper end, it would
-    // overflow the FP32 dual step within about 200 iterations and inf * 0 would turn phi
-    // into NaN (reading Q20).
+  } else if (c.linesearch && d.fnorm == 0.0 && Ppp == 0.0 && Pqq == 0.0) {
+    // Identical gathers (the balanced f identically zero) with p and q identically zero: the
+    // dual move is zero for every step size and every trial would pass, on every iteration.
+    // The step keeps the lower end alpha_k of [alpha_k, alpha_k sqrt(1 + theta_k)] (theta =
+    // 1); growing by the upper end, it would overflow the FP32 dual step within about 200
+    // iterations and inf * 0 would turn phi into NaN (reading Q20).
     o.theta = 1.0;
     o.coef = c.delta * o.alpha;
     o.alpha_f = static_cast<float>(o.alpha);
