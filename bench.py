@@ -673,7 +673,8 @@ def _small_configs_cpu_extra(P, dev, stream, cores, t_iter_3000x400):
     out["hyperbolic_256x64_2000_iterations"] = {
         "gpu_ms": g_ms, "oracle_s": o_s, "oracle_cores": 1,
         "gpu_cell_updates_per_s": nr * nt * K / (g_ms / 1e3), "oracle_cell_updates_per_s": nr * nt * K / o_s,
-        "dist_rel": abs(r.dist - ro["dist"]) / ro["dist"], "gpu_tile": r.tile}
+        "dist_rel": abs(r.dist - ro["dist"]) / ro["dist"], "gpu_tile": r.tile,
+        "note": "GPU and oracle each on their own linesearch decisions (the replayed comparison is in the tests)"}
 
     dt, obs1, preds = synth.shift_sweep_1d(nt=1024)
     O_ = [torch.from_numpy(obs1).to(dev)] * len(preds)
@@ -685,11 +686,13 @@ def _small_configs_cpu_extra(P, dev, stream, cores, t_iter_3000x400):
         t = time.perf_counter()
         res = pool.map(_oracle_shift, [(dt, obs1, q, K) for _, q in preds])
         o_s = time.perf_counter() - t
-    rel = [abs(d - ro_) / ro_ for d, (ro_, _) in zip(dists, res) if ro_ > 0]
+    d_max = max(ro_ for ro_, _ in res)
     out["shift_sweep_1d_61x1024_2000_iterations"] = {
         "gpu_ms": g_ms, "oracle_s": o_s, "oracle_cores": n_proc,
-        "oracle_cpu_s": sum(s_ for _, s_ in res), "max_dist_rel": max(rel),
-        "note": "the 61 shifts in one batched GPU call (one shared-memory-resident CTA each)"}
+        "oracle_cpu_s": sum(s_ for _, s_ in res),
+        "max_dist_diff_over_max_dist": max(abs(d - ro_) for d, (ro_, _) in zip(dists, res)) / d_max,
+        "note": "the 61 shifts in one batched GPU call (one shared-memory-resident CTA each); GPU and "
+                "oracle each on their own linesearch decisions (the replayed comparison is in the tests)"}
 
     obs2, pred2 = synth.gather_pair_transmissive(nt=NT, nr=NR, dt=DT, dx=DX)
     n2 = 20
