@@ -17,7 +17,7 @@ torch.autograd with torch's own copies.
 With N > 1 (launched by torch.distributed.run) the 128 shots are dealt over the ranks
 (largest first, greedy by cells) and every rank solves its share as one batch: the solves
 are independent, so there is no data-path collective (strong scaling, total work fixed).
-The reference arm (--impl reference) times the FP64 CPU oracle on the box's host cores, a
+The reference arm (--impl reference) times the FP64 CPU oracle on the machine's host cores, a
 bounded sample of the same workload per step.  Prints one JSON line on rank 0.
 """
 

@@ -1,6 +1,6 @@
 """The benchmark's reference arm (the FP64 oracle on the host cores) keeps the JSON-line
-contract: one line on stdout with the metric, the value and the keys the driver reads.
-Runs on CPU; the GPU arm's line is produced on a GPU machine."""
+contract: one line on stdout with the metric, the value and the keys its consumers read.
+Runs on CPU; the GPU arm's line needs a GPU."""
 
 import json
 import os
