@@ -642,6 +642,44 @@ def test_batched_autograd_reflective_16x4000x480(pkg):
             assert rel_l2(preds[b].grad.double().cpu().numpy(), g_ref.astype(np.float64)) <= PHI_RTOL
 
 
+def test_host_misfit_matches_device_path_and_oracle(pkg):
+    """emd_misfit_batched_host (host gathers in, distances and adjoint sources out) on five
+    gathers of mixed, ragged sizes, four page-locked and one pageable: the same distances,
+    trial counts and adjoint sources as the device-pointer batched solve plus batched
+    adjoint on the same data, and two sampled gathers equal to the oracle (distance, and
+    adjoint source dx dt (phi - mean phi)) after the same 150 iterations."""
+    dev = torch.device("cuda:0")
+    sizes = [(300, 37, 5), (128, 24, 6), (141, 5, 7), (64, 1, 8), (1000, 9, 9)]
+    pairs = [synth.gather_pair_hyperbolic(nt=nt, nr=nr, seed=sd) for nt, nr, sd in sizes]
+    dts, dxs = [2e-3] * 5, [10.0] * 5
+    h_obs = [torch.from_numpy(o).pin_memory() for o, _ in pairs]
+    h_pred = [torch.from_numpy(p).pin_memory() if b != 2 else torch.from_numpy(p.copy())
+              for b, (_, p) in enumerate(pairs)]
+    assert not h_pred[2].is_pinned()
+    dists, grads, infos = pkg.emd_misfit_host(h_obs, h_pred, dts, dxs, max_iter=150)
+    assert all(i["status"] == 0 and i["iters"] == 150 for i in infos)
+    d_obs = [t.to(dev) for t in h_obs]
+    d_pred = [t.to(dev) for t in h_pred]
+    dd, phis, _ms, dinfos = pkg.emd_batched(d_obs, d_pred, dts, dxs, max_iter=150)
+    gps = [torch.empty_like(t) for t in phis]
+    ws = pkg.new_workspace(pkg.emd_batched_adjoint_workspace_size(5), dev)
+    pkg.emd_adjoint_batched(phis, dts, dxs, pkg.EMD_BAL_MEAN, None, gps, None, ws)
+    torch.cuda.synchronize()
+    for b in range(5):
+        assert infos[b]["ls_trials"] == dinfos[b]["ls_trials"] and infos[b]["tile"] == dinfos[b]["tile"]
+        assert dists[b] == pytest.approx(dd[b], rel=1e-6)
+        assert rel_l2(grads[b].double().numpy(), gps[b].double().cpu().numpy()) <= 1e-5
+    for b in (0, 2):
+        o, p = pairs[b]
+        r = O.pdhg(o, p, dts[b], dxs[b], max_iter=150)
+        g_ref, _ = O.adjoint_source(r["phi"], dts[b], dxs[b])
+        assert dists[b] == pytest.approx(r["dist"], rel=DIST_RTOL)
+        assert rel_l2(grads[b].double().numpy(), g_ref) <= PHI_RTOL
+    only, none, _ = pkg.emd_misfit_host(h_obs, h_pred, dts, dxs, adjoint=False, max_iter=150)
+    assert none is None
+    assert only == pytest.approx(dists, rel=1e-6)
+
+
 def test_marine_shots_sampled(pkg):
     """Two 8000 x 648 streamer gathers (dt = 2 ms, dx = 25 m) solved as one batch: each
     matches the FP64 oracle element-wise after the same 12 iterations."""
