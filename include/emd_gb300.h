@@ -165,7 +165,11 @@ emd_status emd_decompose(const float *f_obs, const float *f_pred, int nt, int nr
  * defaults).  Outputs: phi device [nr][nt] (the dual potential after the last
  * iteration), m device [2][nr][nt] (the flux u), result HOST (required).
  * Iterates are FP32; the linesearch inner products, the stopping residual, the mass
- * sums and the distance accumulate in FP64.  Returns the solve's status (also in
+ * sums and the distance accumulate in FP64.  Algorithm 1 lets alpha_{k+1} be chosen in
+ * [alpha_k, alpha_k sqrt(1 + theta_k)]: the solver takes the upper end, except for
+ * identical gathers (the balanced f identically zero, and with it the dual move for every
+ * step size), where it keeps alpha_k; such a solve returns phi = 0, m = 0 and distance 0
+ * with status EMD_OK at any iteration count.  Returns the solve's status (also in
  * result->status).  Synchronises `stream`.
  */
 emd_status emd_dyn_solve(const float *f_obs, const float *f_pred, int nt, int nr, double dt,
