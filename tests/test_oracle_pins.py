@@ -421,3 +421,18 @@ def test_identical_gathers_keep_the_step_and_stay_finite():
         t = int(q["trace"][0, 2]) - 1  # backtracking steps of the first iteration
         assert q["trace"][0, 0] == pytest.approx(a0 * math.sqrt(2.0) * 0.5 ** t, rel=1e-15)
         assert q["trace"][0, 1] != 1.0
+
+
+def test_exact_fixed_point_keeps_the_upper_end():
+    """Reading Q20's scope: the lower-end step is for identical gathers only.  A 1 x 2 gather
+    pair passes through exact fixed points of the iteration (r_feas = r_step = 0 at iteration
+    112, p and q identically zero with f != 0); it still takes the upper-end trial there, so
+    no iteration has theta = 1."""
+    rng = np.random.default_rng(1002)
+    obs, pred = synth.gather_pair_hyperbolic(nt=8, nr=1, dt=2e-3, seed=3)
+    obs, pred = obs[:, :2].copy(), pred[:, :2].copy()
+    pred += 0.05 * rng.standard_normal(pred.shape).astype(np.float32)
+    r = O.pdhg(obs, pred, 2e-3, 10.0, max_iter=150, record=True)
+    tr = r["trace"]
+    assert ((tr[:, 3] == 0.0) & (tr[:, 4] == 0.0)).any()
+    assert not (tr[:, 1] == 1.0).any()
