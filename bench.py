@@ -620,7 +620,9 @@ def _transmissive_extra(P, dev, stream, a):
     t1, r1 = timed(lambda: P.emd_dyn_solve(o, p, DT, DX, params, phi, m, ws, stream), 3)
     t2, (fr, cr) = timed(lambda: P.emd_dyn_solve_mg(o, p, DT, DX, params, mg, phi, m, ws, stream), 3)
     cells = NT * NR
+    kname, kargs = _kernel_of(r1.tile)
     return {"workload": WORKLOAD, "solves_per_s": 1.0 / t1, "ms_per_solve": 1e3 * t1, "iters": r1.iters,
+            "kernel": f"{kname}{kargs} (tile id {r1.tile}, the autotuner's choice)",
             "cell_updates_per_s": cells * r1.iters / t1, "residual": r1.residual, "dist": r1.dist,
             "two_grid": {"solves_per_s": 1.0 / t2, "ms_per_solve": 1e3 * t2, "factor": MG_FACTOR,
                          "coarse_iters": cr.iters, "fine_iters": fr.iters, "residual": fr.residual,
